@@ -1,0 +1,300 @@
+"""Pins for the oracle's GMRES(m) (Fig. 1; Section 2; Section 5.2).
+
+Every check compares the oracle with something it does not share code with: dense LU
+solves, a dense least-squares minimiser over an explicitly built Krylov space, exact
+termination on matrices with few distinct eigenvalues, closed-form eigenvalues of the
+1D Poisson matrix, the Arnoldi relation, orthogonality, and monotonicity of the GMRES
+residual.  A plausible mistake (dropped term, sign, index, transposed operand) breaks
+at least one of them.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+ALL = ["f64", "f32", "f16", "bf16", "e4m3", "i32", "i16"]
+
+
+def _rand_nonsym(n, seed, shift=3.0):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) / np.sqrt(n) + shift * np.eye(n)
+    return a
+
+
+# --------------------------------------------------------------- dense LU (exact answer)
+@pytest.mark.parametrize("fmt", ALL)
+def test_matches_dense_lu(oracle_lib, fmt):
+    for n, seed in ((5, 1), (17, 2), (40, 3)):
+        a = _rand_nonsym(n, seed)
+        A = W.from_dense(a)
+        b = np.random.default_rng(seed + 10).standard_normal(n)
+        ref = np.linalg.solve(a, b)
+        r = O.gmres(A, b, m=max(n, 8), fmt=O.FORMATS[fmt], tol=1e-13, maxit=4000)
+        assert r["status"] == O.OK, (fmt, n, r["status"], r["true_relres"])
+        assert np.linalg.norm(r["x"] - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_matches_dense_lu_jacobi(oracle_lib):
+    a = _rand_nonsym(30, 4) + np.diag(np.linspace(1, 50, 30))
+    A = W.from_dense(a)
+    b = np.random.default_rng(5).standard_normal(30)
+    r = O.gmres(A, b, m=10, precond=O.PC_JACOBI, tol=1e-13, maxit=2000)
+    assert r["status"] == O.OK
+    ref = np.linalg.solve(a, b)
+    assert np.linalg.norm(r["x"] - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ---------------------------------------- Krylov least squares: x_k = argmin over x0 + K_k
+def _krylov_ls(a, minv, b, x0, k):
+    r0 = b - a @ x0
+    am = a @ minv
+    K = np.empty((a.shape[0], k))
+    v = r0.copy()
+    for i in range(k):
+        K[:, i] = v / np.linalg.norm(v)
+        v = am @ K[:, i]
+    Q, _ = np.linalg.qr(K)
+    c, *_ = np.linalg.lstsq(am @ Q, r0, rcond=None)
+    x = x0 + minv @ (Q @ c)
+    return x, np.linalg.norm(b - a @ x)
+
+
+@pytest.mark.parametrize("precond", [O.PC_NONE, O.PC_JACOBI])
+def test_iterates_are_krylov_minimisers(oracle_lib, precond):
+    n = 30
+    a = _rand_nonsym(n, 6, shift=2.0) + np.diag(np.linspace(0.5, 4, n))
+    A = W.from_dense(a)
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(n); x0 = rng.standard_normal(n) * 0.1
+    minv = np.diag(1.0 / np.diag(a)) if precond == O.PC_JACOBI else np.eye(n)
+    bn = np.linalg.norm(b)
+    for k in range(1, 9):
+        r = O.gmres(A, b, x0, m=20, precond=precond, tol=0.0, maxit=k, want_H1=True,
+                    hist_cap=k)
+        xk, resk = _krylov_ls(a, minv, b, x0, k)
+        assert r["iters"] == k
+        assert np.linalg.norm(r["x"] - xk) <= 1e-10 * np.linalg.norm(xk)
+        # Givens recurrence residual equals the dense least-squares residual
+        assert abs(r["hist"][k - 1] - resk / bn) <= 1e-12
+
+
+def test_poisson2d_recurrence_matches_dense_krylov_ls(oracle_lib):
+    A = W.poisson2d(16)
+    a = A.dense()
+    b = W.rhs_sin(A.n)
+    r = O.gmres(A, b, m=50, tol=0.0, maxit=8, hist_cap=8)
+    for k in range(1, 9):
+        _, resk = _krylov_ls(a, np.eye(A.n), b, np.zeros(A.n), k)
+        assert abs(r["hist"][k - 1] - resk / np.linalg.norm(b)) <= 1e-12
+
+
+# ------------------------------------------------------------------- exact termination
+def test_identity_converges_in_one_step(oracle_lib):
+    A = W.from_dense(np.eye(12))
+    b = np.arange(1.0, 13.0)
+    r = O.gmres(A, b, m=5, tol=1e-14)
+    assert r["status"] == O.OK and r["iters"] == 1
+    assert np.allclose(r["x"], b, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_k_distinct_eigenvalues_terminate_in_k_steps(oracle_lib, k):
+    n = 25
+    rng = np.random.default_rng(k)
+    eig = np.arange(1, k + 1, dtype=float)[rng.integers(0, k, n)]
+    eig[:k] = np.arange(1, k + 1)          # every eigenvalue present
+    S = np.eye(n) + 0.3 * np.triu(rng.standard_normal((n, n)), 1)
+    a = S @ np.diag(eig) @ np.linalg.inv(S)   # nonsymmetric, k distinct eigenvalues
+    A = W.from_dense(a)
+    b = rng.standard_normal(n)
+    r = O.gmres(A, b, m=20, tol=1e-11, maxit=200, want_H1=True)
+    assert r["status"] == O.OK
+    assert r["k1"] <= k                      # first cycle ends by breakdown or convergence
+    assert np.linalg.norm(r["x"] - np.linalg.solve(a, b)) <= 1e-9 * np.linalg.norm(r["x"])
+
+
+# ------------------------------------------- 1D Poisson: closed-form eigenvalues (Lanczos)
+def test_poisson1d_hessenberg_eigenvalues_closed_form(oracle_lib):
+    n = 20
+    a = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    A = W.from_dense(a)
+    b = np.random.default_rng(11).standard_normal(n)
+    r = O.gmres(A, b, m=n, tol=0.0, maxit=n, want_H1=True)
+    k = r["k1"]
+    assert k == n
+    H = r["H1"][:k, :k]
+    # symmetric A: the Hessenberg is tridiagonal and symmetric (Lanczos)
+    assert np.max(np.abs(np.triu(H, 2))) <= 1e-12
+    assert np.allclose(np.diag(H, 1), np.diag(H, -1), rtol=1e-10, atol=1e-12)
+    lam = np.sort(np.linalg.eigvals(H).real)
+    exact = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))
+    assert np.max(np.abs(lam - exact)) <= 1e-10
+
+
+# ------------------------------------------------------- Arnoldi relation, orthogonality
+_DELTA = {"f64": (0.0, 0.0), "f32": (2.0 ** -24, 0.0), "f16": (2.0 ** -11, 2.0 ** -25),
+          "bf16": (2.0 ** -8 + 2.0 ** -24, 0.0), "e4m3": (2.0 ** -4 + 2.0 ** -24, None),
+          "i32": (0.0, None), "i16": (0.0, None)}
+
+
+@pytest.mark.parametrize("fmt", ALL)
+def test_arnoldi_relation(oracle_lib, fmt):
+    A = W.convdiff3d(6)
+    a = A.dense()
+    b = W.rhs_sin(A.n)
+    k = 25
+    r = O.gmres(A, b, m=k, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True, want_V1=True)
+    V = r["V1"]; H = r["H1"][: k + 1, :k]
+    assert V.shape[1] == k + 1
+    E = a @ V[:, :k] - V @ H
+    rel, absq = _DELTA[fmt]
+    nA = np.linalg.norm(a, 2)
+    for j in range(k):
+        hn = H[j + 1, j]
+        vj1 = V[:, j + 1]
+        if absq is None:   # scaled formats: half the quantum of the stored vector
+            if fmt in ("i32", "i16"):
+                q = np.min(np.abs(vj1[vj1 != 0])) if np.any(vj1) else 0.0
+                mx = 32767 if fmt == "i16" else 2147483647
+                sigma = np.max(np.abs(vj1)) / mx
+                bound_v = 0.5 * sigma * np.sqrt(A.n) * 1.0001
+            else:
+                s = 2.0 ** np.ceil(np.log2(np.max(np.abs(vj1)) / 448.0))
+                bound_v = rel * 1.0 + 0.5 * 2.0 ** -9 * s * np.sqrt(A.n)
+        else:
+            bound_v = rel + absq * np.sqrt(A.n)
+        assert np.linalg.norm(E[:, j]) <= hn * bound_v * 1.01 + 1e-13 * nA, (j, fmt)
+
+
+def test_orthogonality_f64_cgs2(oracle_lib):
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    r = O.gmres(A, b, m=60, tol=0.0, maxit=60, want_V1=True)
+    V = r["V1"]
+    assert np.linalg.norm(np.eye(V.shape[1]) - V.T @ V, 2) <= 1e-13
+
+
+@pytest.mark.parametrize("fmt,bound", [("f32", 1e-6), ("i32", 1e-8), ("f16", 5e-3), ("i16", 5e-4)])
+def test_orthogonality_compressed(oracle_lib, fmt, bound):
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    r = O.gmres(A, b, m=40, fmt=O.FORMATS[fmt], tol=0.0, maxit=40, want_V1=True)
+    V = r["V1"]
+    assert np.linalg.norm(np.eye(V.shape[1]) - V.T @ V, 2) <= bound
+
+
+# -------------------------------------------------------------- residual behaviour
+@pytest.mark.parametrize("fmt", ["f64", "f16", "i16"])
+def test_recurrence_residual_monotone_within_cycle(oracle_lib, fmt):
+    A = W.convdiff3d(10)
+    b = W.rhs_sin(A.n)
+    m = 15
+    r = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=1e-10, maxit=600, hist_cap=600, tres_cap=100)
+    h = r["hist"]
+    for c0 in range(0, len(h), m):
+        seg = h[c0:c0 + m]
+        assert np.all(np.diff(seg) <= 1e-15 * seg[0])
+
+
+def test_explicit_equals_recurrence_residual_f64(oracle_lib):
+    A = W.convdiff3d(10)
+    b = W.rhs_sin(A.n)
+    r = O.gmres(A, b, m=200, tol=1e-10, maxit=1000, hist_cap=1000)
+    assert r["status"] == O.OK and r["cycles"] == 1
+    assert abs(r["true_relres"] - r["hist"][-1]) <= 1e-13
+
+
+def test_restarts_continue_from_explicit_residual(oracle_lib):
+    A = W.poisson2d(32)
+    xs = W.exact_solution(A.n, 1)
+    b = W.rhs_from_solution(A, xs)
+    r = O.gmres(A, b, m=10, tol=1e-8, maxit=5000, tres_cap=1000)
+    assert r["status"] == O.OK and r["cycles"] > 3
+    t = r["tres"]
+    assert t[0] == pytest.approx(1.0) and t[-1] <= 1e-8
+    assert np.all(np.diff(t) <= 1e-15)    # GMRES never increases the residual norm
+
+
+# -------------------------------------------------------------- reorthogonalisation modes
+def test_reorth_modes(oracle_lib):
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    ra = O.gmres(A, b, m=30, tol=1e-10, maxit=3000, reorth=O.REORTH_ALWAYS)
+    rc = O.gmres(A, b, m=30, tol=1e-10, maxit=3000, reorth=O.REORTH_CONDITIONAL)
+    rn = O.gmres(A, b, m=30, tol=1e-10, maxit=3000, reorth=O.REORTH_NEVER)
+    for r in (ra, rc, rn):
+        assert r["status"] == O.OK and r["true_relres"] <= 1e-10
+    assert ra["reorths"] == ra["iters"]
+    assert 0 <= rc["reorths"] <= rc["iters"]
+    assert rn["reorths"] == 0
+
+
+def test_literal_fig1_clause_truncates_cycles(oracle_lib):
+    """Reading R2: the printed second clause of Fig. 1 step 12 ends a cycle as soon as
+    h_{j+1,j} < eta * omega; on this problem that happens within the first steps."""
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    r_lit = O.gmres(A, b, m=30, tol=1e-10, maxit=30, reorth=O.REORTH_CONDITIONAL,
+                    literal_fig1=True)
+    r_brk = O.gmres(A, b, m=30, tol=1e-10, maxit=30, reorth=O.REORTH_CONDITIONAL)
+    assert r_lit["k1"] < 30 <= r_brk["k1"] or r_lit["k1"] < r_brk["k1"]
+
+
+# ------------------------------------------------------------------------- edge cases
+def test_zero_rhs_gives_zero(oracle_lib):
+    A = W.poisson2d(4)
+    r = O.gmres(A, np.zeros(A.n), np.ones(A.n), m=5)
+    assert r["status"] == O.OK and r["iters"] == 0 and np.all(r["x"] == 0)
+
+
+def test_exact_initial_guess(oracle_lib):
+    A = W.poisson2d(4)
+    xs = np.arange(A.n, dtype=float)
+    b = O.spmv(A, xs)
+    r = O.gmres(A, b, xs, m=5)
+    assert r["status"] == O.OK and r["iters"] == 0
+
+
+def test_n_equals_one(oracle_lib):
+    A = W.from_dense(np.array([[4.0]]))
+    r = O.gmres(A, np.array([2.0]), m=3)
+    assert r["status"] == O.OK and r["iters"] == 1 and r["x"][0] == 0.5
+
+
+def test_maxit_limits_and_reports(oracle_lib):
+    A = W.poisson2d(16)
+    b = W.rhs_sin(A.n)
+    r = O.gmres(A, b, m=10, tol=1e-12, maxit=7)
+    assert r["status"] == O.NOT_CONVERGED and r["iters"] == 7
+    r0 = O.gmres(A, b, m=10, tol=1e-12, maxit=0)
+    assert r0["status"] == O.NOT_CONVERGED and r0["iters"] == 0
+
+
+def test_nonfinite_input(oracle_lib):
+    A = W.poisson2d(4)
+    b = np.ones(A.n); b[3] = np.nan
+    assert O.gmres(A, b, m=5)["status"] == O.ERR_NONFINITE
+
+
+def test_jacobi_zero_diagonal_is_an_argument_error(oracle_lib):
+    a = np.array([[0.0, 1.0], [1.0, 0.0]])
+    A = W.from_dense(a)
+    assert O.gmres(A, np.ones(2), m=2, precond=O.PC_JACOBI)["status"] == O.ERR_ARG
+
+
+# --------------------------------------------------- Section 5.2 protocol (qualitative)
+def test_paper_protocol_32bit_formats_match_f64(oracle_lib):
+    """b_i = sin(i), x0 = 0, m = 100, tau = 1e-9 (Section 5.2).  Table 2 reports the
+    32-bit formats close to the FP64 iteration count (mean ratio 1.02): qualitative
+    only -- a 32-bit basis may need one extra restart to turn a converged recurrence
+    residual into a converged true residual (Section 5.2), which is what happens here."""
+    A = W.convdiff3d(12)
+    b = W.rhs_sin(A.n)
+    its = {}
+    for fmt in ("f64", "f32", "i32"):
+        r = O.gmres(A, b, m=100, fmt=O.FORMATS[fmt], precond=O.PC_JACOBI, tol=1e-9, maxit=5000)
+        assert r["status"] == O.OK and r["true_relres"] <= 1e-9
+        its[fmt] = r["iters"]
+    assert its["f64"] <= its["f32"] <= 1.25 * its["f64"]
+    assert its["f64"] <= its["i32"] <= 1.25 * its["f64"]
