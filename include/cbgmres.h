@@ -1,0 +1,198 @@
+/*
+ * cbgmres.h -- C ABI of the GB300 (sm_103a) compressed-basis GMRES library.
+ *
+ * Method: Aliaga, Anzt, Gruetzmacher, Quintana-Orti, Tomas, "Compressed Basis GMRES on
+ * High Performance GPUs" (arXiv 2009.12101).  Restarted, right-preconditioned GMRES(m)
+ * (Fig. 1) whose Krylov basis V is stored in a compact format while the arithmetic
+ * keeps FP64 accuracy (Section 3); the basis is decompressed on every read and
+ * compressed on every store (Section 4.2, "memory accessor"); fixed-point formats carry
+ * the per-vector scale sigma_j = (||v_j||_inf / ||v_j||_2) / max_intxx (Section 4.2);
+ * convergence ||b - A x||_2 <= tau ||b||_2 is confirmed by an explicit residual each
+ * time the recurrence residual says so (Section 5.2).
+ *
+ * Conventions for every entry point
+ *   - Plain pointers and sizes; no library types cross the boundary except the opaque
+ *     handles and the option/statistics structs below.
+ *   - "device" pointers are CUDA device addresses of the current device; "host"
+ *     pointers are ordinary CPU memory.  Vectors are dense FP64 arrays of length n.
+ *   - All work is enqueued on options.stream (a cudaStream_t, NULL = legacy default
+ *     stream); calls that return results to the host synchronise that stream.
+ *   - Every function returns an int status (CBG_OK = 0).  Positive values are
+ *     non-fatal (x still holds the best iterate); negative values are errors and leave
+ *     outputs unspecified.  Nothing throws across the ABI.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef CBGMRES_H
+#define CBGMRES_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- storage formats of the Krylov basis (Section 4.2; bf16/e4m3 are additions) ---- */
+typedef enum {
+    CBG_F64 = 0,   /* IEEE double                                                   */
+    CBG_F32 = 1,   /* IEEE single, round-to-nearest cast                           */
+    CBG_F16 = 2,   /* IEEE half, one round-to-nearest-even of the FP64 value       */
+    CBG_BF16 = 3,  /* bfloat16 of v / 2^e, per-vector power-of-two scale 2^e       */
+    CBG_E4M3 = 4,  /* OCP FP8 E4M3 of v / 2^e, saturating, power-of-two scale 2^e  */
+    CBG_I32 = 5,   /* fixed point, code = rint(v / sigma), sigma = max|v| / (2^31-1) */
+    CBG_I16 = 6    /* fixed point, code = rint(v / sigma), sigma = max|v| / (2^15-1) */
+} cbg_format;
+
+typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2 } cbg_precond;
+typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
+
+/* Arithmetic of the basis products (Fig. 1 steps 5, 8, 17).
+ * CBG_ARITH_DF32: products and partial sums in double-float (pairs of FP32 with
+ *   error-free transformations, >= 44-bit effective significand per partial chain),
+ *   cross-thread and cross-block combination in FP64.  GB300's FP64 pipe issues about
+ *   1/70 of its FP32 rate, so this is the mode that streams the basis at HBM speed.
+ * CBG_ARITH_FP64: every product and sum is a native FP64 operation, as the paper
+ *   prescribes; on GB300 the basis products then run at FP64-pipe speed.
+ * SpMV, norms, Givens rotations, the least-squares solve and the solution update are
+ * FP64 in both modes. */
+typedef enum { CBG_ARITH_DF32 = 0, CBG_ARITH_FP64 = 1 } cbg_arith;
+
+/* status codes */
+#define CBG_OK                 0
+#define CBG_NOT_CONVERGED      1   /* maxit Arnoldi steps done, tau not reached        */
+#define CBG_ERR_ARG          (-1)  /* invalid argument                                 */
+#define CBG_ERR_NONFINITE    (-2)  /* NaN/Inf in the data or produced by the iteration */
+#define CBG_ERR_OOM          (-3)  /* device allocation failed                         */
+#define CBG_ERR_CUDA         (-4)  /* a CUDA call failed                               */
+#define CBG_ERR_TIMEOUT      (-5)  /* a bounded device-side wait ran out               */
+#define CBG_ERR_UNSUPPORTED  (-6)  /* combination not implemented                      */
+
+/* Sparse matrix in CSR form: row_ptr[n+1] (int32, row_ptr[0] = 0), col[nnz] (int32,
+ * 0-based), val[nnz] (FP64).  on_device != 0: the three arrays are device pointers,
+ * otherwise host pointers.  cbgmres_create deep-copies them; the caller keeps
+ * ownership and may free them once create returns. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+    int32_t on_device;
+    int32_t pad0;
+} cbg_csr;
+
+typedef struct {
+    int32_t reorth;          /* cbg_reorth, default CBG_REORTH_ALWAYS (CGS + 1 pass)   */
+    int32_t precond;         /* cbg_precond, default CBG_PC_NONE                       */
+    int32_t arith;           /* cbg_arith, default CBG_ARITH_DF32                      */
+    int32_t spmv_group;      /* lanes per CSR row: 0 = automatic, else 1..32 (pow2)   */
+    double eta;              /* conditional re-orthogonalisation threshold (1/sqrt 2)  */
+    double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
+    void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
+    int32_t check_every;     /* host polls the convergence flag every k steps (4)      */
+    int32_t use_graph;       /* 1: replay the Arnoldi steps from CUDA graphs (1)       */
+} cbg_options;
+
+typedef struct {
+    int64_t iters;           /* Arnoldi steps (sparse products of Fig. 1 step 3)       */
+    int64_t restarts;        /* restart cycles started                                 */
+    int64_t reorths;         /* re-orthogonalisation passes                            */
+    double true_relres;      /* ||b - A x||_2 / ||b||_2 at exit (FP64, explicit)       */
+    double est_relres;       /* last recurrence residual |g_{j+1}| / ||b||_2           */
+    double ms_total;         /* wall time of the solve on the stream (CUDA events)     */
+    double bytes_model;      /* model HBM bytes: SpMV + 4 basis passes per step         */
+    int32_t status;          /* same value as the function's return                    */
+    int32_t pad0;
+    double* history;         /* optional host buffer: recurrence residual per step     */
+    int64_t history_cap;     /* its capacity (0: none)                                  */
+    int64_t history_len;     /* entries written                                         */
+} cbg_stats;
+
+typedef struct cbg_handle cbg_handle;
+typedef struct cbg_batch cbg_batch;
+
+/* Fill *opt with the defaults listed above. */
+void cbgmres_options_default(cbg_options* opt);
+
+/* Human-readable text of a status code (static storage). */
+const char* cbgmres_status_string(int status);
+
+/* Bytes per stored basis element of `fmt` (8, 4, 2 or 1), 0 for an invalid format. */
+int cbgmres_format_bytes(int fmt);
+
+/* Create a solver for A with restart length `restart` (basis dimension m, Fig. 1) and
+ * basis format `fmt`.  Copies A to library-owned device memory and allocates the basis
+ * V ((m+1) columns of n codes, each column 2048-element padded), the per-vector scales,
+ * the Hessenberg and the work vectors once; every solve reuses them.
+ * Errors: CBG_ERR_ARG (n < 1, restart < 1, bad format, bad CSR bounds when the CSR is
+ * on the host), CBG_ERR_OOM, CBG_ERR_CUDA.  *out is NULL on error. */
+int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* opt,
+                   cbg_handle** out);
+
+/* Right preconditioner z = P v with P on A's sparsity pattern (learned sparse
+ * approximate inverse); pvals[nnz] in A's CSR order, FP64, device (on_device != 0) or
+ * host.  Takes effect when options.precond == CBG_PC_SPAI.  Errors: CBG_ERR_ARG. */
+int cbgmres_set_spai(cbg_handle* h, const double* pvals, int on_device);
+
+/* Solve A x = b.  b, x: device pointers (length n).  x holds x0 on entry and the
+ * final iterate on exit.  Stops when ||b - A x|| <= tol ||b|| (explicit residual,
+ * Section 5.2) or after maxit Arnoldi steps (CBG_NOT_CONVERGED).  stats may be NULL.
+ * Synchronises options.stream once per restart (to read the explicit residual). */
+int cbgmres_solve(cbg_handle* h, const double* b, double* x, double tol, int64_t maxit,
+                  cbg_stats* stats);
+
+/* As cbgmres_solve with host b and x: copies b and x0 to the device on the stream,
+ * solves, copies x back.  For callers without device buffers. */
+int cbgmres_solve_host(cbg_handle* h, const double* b_host, double* x_host, double tol,
+                       int64_t maxit, cbg_stats* stats);
+
+/* Run k Arnoldi steps of the first restart cycle from x0 (device b, x0) and copy the
+ * raw (k+1) x k Hessenberg (before Givens rotations, column-major, leading dimension
+ * k+1) to H_host.  *k_done receives the number of columns produced (< k on breakdown).
+ * Used to check parity of the orthogonalisation (Fig. 1 steps 3-14). */
+int cbgmres_arnoldi(cbg_handle* h, const double* b, const double* x0, int k,
+                    double* H_host, int* k_done);
+
+/* Decoded basis column `col` of the last run (FP64, device out[n]).  Test access to
+ * what the accessor returns (Section 4.2). */
+int cbgmres_basis_column(cbg_handle* h, int col, double* out);
+
+void cbgmres_destroy(cbg_handle* h);
+
+/* ---- codec kernels (Section 4.2 accessor), exposed for bit-exact parity checks ----
+ * Encode a normalised FP64 vector v (device, length n) whose largest magnitude is vmax
+ * into codes (device, n elements of cbgmres_format_bytes(fmt) bytes); *scale_out gets
+ * the decode scale (sigma, 2^e, or 1).  Decode multiplies back into FP64 out (device).
+ * Synchronises `stream`. */
+int cbg_encode(int fmt, int64_t n, const double* v, double vmax, void* codes,
+               double* scale_out, void* stream);
+int cbg_decode(int fmt, int64_t n, const void* codes, double scale, double* out,
+               void* stream);
+
+/* ---- basis products, exposed for parity checks (Fig. 1 steps 5 and 8) -------------
+ * V: device codes, ncols columns of leading dimension ld elements; scales[ncols] host.
+ * cbg_basis_dot:  h[k] = sum_i dec(V[i,k]) w[i]      (h: host, w: device)
+ * cbg_basis_axpy: w[i] -= sum_k dec(V[i,k]) h[k]     (h: host, w: device, in place)
+ * arith: cbg_arith.  Synchronise `stream`. */
+int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
+                  const double* scales, const double* w, double* h, void* stream);
+int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
+                   const double* scales, const double* h, double* w, void* stream);
+
+/* y = A x with the library's SpMV (device x, y).  For parity checks. */
+int cbgmres_spmv(cbg_handle* h, const double* x, double* y);
+
+/* ---- batched solve (many independent systems, one persistent launch) ---------------
+ * nsys systems As[s] (host or device CSR per on_device), all with restart `restart` and
+ * format `fmt`.  One persistent kernel runs whole GMRES(m) solves, one thread block per
+ * system taken from a device work queue ordered by decreasing size; the launch is
+ * replayed from a CUDA graph.  Per-system x (device) holds x0 on entry. */
+int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt,
+                           const cbg_options* opt, cbg_batch** out);
+int cbgmres_solve_batched(cbg_batch* bt, const double* const* b, double* const* x,
+                          double tol, int64_t maxit, cbg_stats* per_sys);
+void cbgmres_destroy_batched(cbg_batch* bt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,302 @@
+"""GB300 compressed-basis GMRES (CB-GMRES, arXiv 2009.12101) -- thin Python binding.
+
+Every step of the solver runs in the CUDA library ``_lib/libcbgmres.so`` (C ABI in
+``include/cbgmres.h``).  This module only marshals arguments: it hands device pointers
+of torch tensors and the current CUDA stream to the library.  There is no CPU
+fallback: if the library is missing or no GPU is visible the calls raise.
+
+    import paper_2009_12101_gb300 as cb
+    s = cb.Solver(rowptr, col, val, restart=100, fmt="f32")
+    stats = s.solve(b, x, tol=1e-10, maxit=20000)    # b, x: CUDA float64 tensors
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build as _build
+
+FORMATS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "i32": 5, "i16": 6}
+FORMAT_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i16": 2}
+PRECONDS = {"none": 0, "jacobi": 1, "spai": 2}
+REORTH = {"always": 0, "conditional": 1, "never": 2}
+ARITH = {"df32": 0, "fp64": 1}
+STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM",
+          -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_UNSUPPORTED"}
+TILE_ROWS = 4096   # padded rows per basis column (multiple of every kernel tile)
+
+
+class CbgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: status {status} ({STATUS.get(status, '?')})")
+        self.status = status
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32), ("pad0", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("reorth", C.c_int32), ("precond", C.c_int32), ("arith", C.c_int32),
+                ("spmv_group", C.c_int32), ("eta", C.c_double), ("breakdown_eps", C.c_double),
+                ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("reorths", C.c_int64),
+                ("true_relres", C.c_double), ("est_relres", C.c_double), ("ms_total", C.c_double),
+                ("bytes_model", C.c_double), ("status", C.c_int32), ("pad0", C.c_int32),
+                ("history", C.c_void_p), ("history_cap", C.c_int64), ("history_len", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def ensure_built() -> str:
+    """Compile libcbgmres.so for sm_103a if it is missing or older than its sources."""
+    return _build()
+
+
+def lib():
+    """Load libcbgmres.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                                  "paper_2009_12101_gb300.ensure_built() (needs nvcc)")
+            L = C.CDLL(_LIB_PATH)
+            vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int, C.c_double
+            L.cbgmres_options_default.argtypes = [C.POINTER(Options)]
+            L.cbgmres_options_default.restype = None
+            L.cbgmres_status_string.argtypes = [i32]
+            L.cbgmres_status_string.restype = C.c_char_p
+            L.cbgmres_format_bytes.argtypes = [i32]
+            L.cbgmres_create.argtypes = [C.POINTER(Csr), i32, i32, C.POINTER(Options), C.POINTER(vp)]
+            L.cbgmres_set_spai.argtypes = [vp, vp, i32]
+            L.cbgmres_solve.argtypes = [vp, vp, vp, d, i64, C.POINTER(Stats)]
+            L.cbgmres_solve_host.argtypes = [vp, vp, vp, d, i64, C.POINTER(Stats)]
+            L.cbgmres_arnoldi.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_int)]
+            L.cbgmres_basis_column.argtypes = [vp, i32, vp]
+            L.cbgmres_spmv.argtypes = [vp, vp, vp]
+            L.cbgmres_destroy.argtypes = [vp]
+            L.cbgmres_destroy.restype = None
+            L.cbg_encode.argtypes = [i32, i64, vp, d, vp, C.POINTER(d), vp]
+            L.cbg_decode.argtypes = [i32, i64, vp, d, vp, vp]
+            L.cbg_basis_dot.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.cbg_basis_axpy.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.cbgmres_create_batched.argtypes = [i32, vp, i32, i32, C.POINTER(Options), C.POINTER(vp)]
+            L.cbgmres_solve_batched.argtypes = [vp, vp, vp, d, i64, vp]
+            L.cbgmres_destroy_batched.argtypes = [vp]
+            L.cbgmres_destroy_batched.restype = None
+            _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("CB-GMRES needs a CUDA GPU (no device visible)")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc < 0:
+        raise CbgError(rc, where)
+    return rc
+
+
+def _dev_f64(t, n=None, name="vector"):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    return C.c_void_p(t.data_ptr())
+
+
+def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=None,
+            check_every=4, eta=None, breakdown_eps=None) -> Options:
+    o = Options()
+    lib().cbgmres_options_default(C.byref(o))
+    o.precond = PRECONDS[precond]
+    o.arith = ARITH[arith]
+    o.reorth = REORTH[reorth]
+    o.spmv_group = spmv_group
+    o.check_every = check_every
+    if eta is not None:
+        o.eta = eta
+    if breakdown_eps is not None:
+        o.breakdown_eps = breakdown_eps
+    o.stream = _stream_ptr(stream).value
+    return o
+
+
+def _stats_dict(st: Stats, hist=None) -> dict:
+    out = {k: getattr(st, k) for k in ("iters", "restarts", "reorths", "true_relres", "est_relres",
+                                       "ms_total", "bytes_model", "status")}
+    if hist is not None:
+        out["history"] = hist[: st.history_len].copy()
+    return out
+
+
+class Solver:
+    """Handle on libcbgmres for one matrix, restart length and basis format.
+
+    rowptr/col/val: CSR arrays (int32, int32, float64) as numpy arrays (copied from
+    host) or CUDA tensors (copied device to device)."""
+
+    def __init__(self, rowptr, col, val, *, restart: int = 100, fmt: str = "f64",
+                 precond: str = "none", arith: str = "df32", reorth: str = "always",
+                 spmv_group: int = 0, stream=None, check_every: int = 4):
+        torch = _torch()
+        L = lib()
+        self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
+        self.stream = stream
+        keep = []
+        if isinstance(rowptr, torch.Tensor):
+            rp = rowptr.to(torch.int32).contiguous(); ci = col.to(torch.int32).contiguous()
+            va = val.to(torch.float64).contiguous(); keep += [rp, ci, va]
+            csr = Csr(rp.numel() - 1, ci.numel(), rp.data_ptr(), ci.data_ptr(), va.data_ptr(), 1, 0)
+        else:
+            rp = np.ascontiguousarray(rowptr, np.int32); ci = np.ascontiguousarray(col, np.int32)
+            va = np.ascontiguousarray(val, np.float64); keep += [rp, ci, va]
+            csr = Csr(rp.size - 1, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, 0)
+        self.n, self.nnz = int(csr.n), int(csr.nnz)
+        self.ld = (self.n + TILE_ROWS - 1) // TILE_ROWS * TILE_ROWS
+        opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
+                      stream=stream, check_every=check_every)
+        h = C.c_void_p()
+        _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
+               "cbgmres_create")
+        self._h = h
+
+    @classmethod
+    def from_csr(cls, A, **kw):
+        """A: any object with rowptr, col, val arrays (e.g. workloads.CSR)."""
+        return cls(A.rowptr, A.col, A.val, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cbgmres_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_spai(self, pvals):
+        torch = _torch()
+        if isinstance(pvals, torch.Tensor):
+            p = pvals.to(torch.float64).contiguous()
+            _check(lib().cbgmres_set_spai(self._h, C.c_void_p(p.data_ptr()), 1), "cbgmres_set_spai")
+        else:
+            p = np.ascontiguousarray(pvals, np.float64)
+            _check(lib().cbgmres_set_spai(self._h, C.c_void_p(p.ctypes.data), 0), "cbgmres_set_spai")
+
+    def solve(self, b, x, tol: float = 1e-10, maxit: int = 100000, history: int = 0) -> dict:
+        """b, x: CUDA float64 tensors (x: initial guess in, solution out)."""
+        st = Stats()
+        hist = None
+        if history:
+            hist = np.zeros(history); st.history = hist.ctypes.data; st.history_cap = history
+        rc = lib().cbgmres_solve(self._h, _dev_f64(b, self.n, "b"), _dev_f64(x, self.n, "x"),
+                                 tol, maxit, C.byref(st))
+        _check(rc, "cbgmres_solve")
+        return _stats_dict(st, hist)
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, tol: float = 1e-10, maxit: int = 100000) -> dict:
+        """b, x: host float64 arrays; host<->device copies happen inside the call."""
+        b = np.ascontiguousarray(b, np.float64)
+        if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+            raise TypeError("x must be a contiguous float64 numpy array")
+        st = Stats()
+        rc = lib().cbgmres_solve_host(self._h, C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data),
+                                      tol, maxit, C.byref(st))
+        _check(rc, "cbgmres_solve_host")
+        return _stats_dict(st)
+
+    def arnoldi(self, b, x0, k: int) -> np.ndarray:
+        """Raw (k+1) x k Hessenberg of the first k Arnoldi steps from x0."""
+        H = np.zeros((k, k + 1))
+        kd = C.c_int()
+        _check(lib().cbgmres_arnoldi(self._h, _dev_f64(b, self.n, "b"), _dev_f64(x0, self.n, "x0"),
+                                     k, C.c_void_p(H.ctypes.data), C.byref(kd)), "cbgmres_arnoldi")
+        kd = kd.value
+        flat = H.ravel()[: (kd + 1) * kd]
+        return flat.reshape(kd, kd + 1).T.copy()
+
+    def basis_column(self, col: int):
+        torch = _torch()
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(lib().cbgmres_basis_column(self._h, col, C.c_void_p(out.data_ptr())),
+               "cbgmres_basis_column")
+        return out
+
+    def spmv(self, x):
+        torch = _torch()
+        y = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(lib().cbgmres_spmv(self._h, _dev_f64(x, self.n, "x"), C.c_void_p(y.data_ptr())),
+               "cbgmres_spmv")
+        return y
+
+
+# ------------------------------------------------------------------ codec / kernel access
+CODE_TORCH = {"f64": "float64", "f32": "float32", "f16": "int16", "bf16": "int16", "e4m3": "uint8",
+              "i32": "int32", "i16": "int16"}
+
+
+def encode(fmt: str, v, vmax: float, stream=None):
+    """Encode a normalised CUDA float64 vector; returns (codes tensor, scale)."""
+    torch = _torch()
+    codes = torch.empty(v.numel(), dtype=getattr(torch, CODE_TORCH[fmt]), device=v.device)
+    scale = C.c_double()
+    _check(lib().cbg_encode(FORMATS[fmt], v.numel(), _dev_f64(v), vmax, C.c_void_p(codes.data_ptr()),
+                            C.byref(scale), _stream_ptr(stream)), "cbg_encode")
+    return codes, scale.value
+
+
+def decode(fmt: str, codes, scale: float, stream=None):
+    torch = _torch()
+    out = torch.empty(codes.numel(), dtype=torch.float64, device=codes.device)
+    _check(lib().cbg_decode(FORMATS[fmt], codes.numel(), C.c_void_p(codes.data_ptr()), scale,
+                            C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "cbg_decode")
+    return out
+
+
+def basis_dot(fmt: str, arith: str, n: int, V, ld: int, scales, w, stream=None) -> np.ndarray:
+    """h = V^T w for a code matrix V (CUDA tensor, ncols x ld codes)."""
+    ncols = V.shape[0]
+    h = np.zeros(ncols)
+    sc = np.ascontiguousarray(scales, np.float64)
+    _check(lib().cbg_basis_dot(FORMATS[fmt], ARITH[arith], n, ncols, C.c_void_p(V.data_ptr()), ld,
+                               C.c_void_p(sc.ctypes.data), _dev_f64(w), C.c_void_p(h.ctypes.data),
+                               _stream_ptr(stream)), "cbg_basis_dot")
+    return h
+
+
+def basis_axpy(fmt: str, arith: str, n: int, V, ld: int, scales, h, w, stream=None):
+    """w -= V h in place (w: CUDA float64 tensor of ld elements)."""
+    ncols = V.shape[0]
+    sc = np.ascontiguousarray(scales, np.float64)
+    hh = np.ascontiguousarray(h, np.float64)
+    _check(lib().cbg_basis_axpy(FORMATS[fmt], ARITH[arith], n, ncols, C.c_void_p(V.data_ptr()), ld,
+                                C.c_void_p(sc.ctypes.data), C.c_void_p(hh.ctypes.data), _dev_f64(w),
+                                _stream_ptr(stream)), "cbg_basis_axpy")
+    return w

@@ -1,0 +1,607 @@
+// cbg_kernels.cuh -- CUDA kernels of the restarted Arnoldi step (Fig. 1 steps 3-14),
+// templated on the basis storage format and on the arithmetic mode.
+//
+// Data layout in HBM (per solver handle):
+//   V       (m+1) columns of codes, column k at V + k*ldb, ldb = ld * bytes(fmt),
+//           ld = n rounded up to TILE_ROWS; rows n..ld-1 are zero and stay zero, so every
+//           kernel processes whole tiles without bounds checks on the basis.
+//   scales  (m+1) FP64 decode factors (sigma_k, 2^e_k or 1)
+//   vectors FP64 arrays of ld elements, zero padded.
+#pragma once
+#include "cbg_device.cuh"
+
+namespace cbg {
+
+constexpr int THREADS = 256;
+constexpr int TILE_ROWS = 4096;      // ld (padded rows) is a multiple of this
+constexpr int DOT_TR = 1024;         // rows of w staged in shared memory per dot tile
+constexpr int MAXCOLS = 256;         // largest restart length + 1 supported by the kernels
+constexpr int ARITH_DF32 = 0;
+constexpr int ARITH_FP64 = 1;
+
+// Solver state shared by the kernels of one handle (device memory).
+struct DevState {
+    int active;           // 1 while the current restart cycle continues
+    int k;                // Hessenberg columns completed in the cycle
+    int stop;             // 0 running, 1 recurrence converged, 2 breakdown, 3 non-finite, 4 kcap
+    int kcap;             // steps allowed in this cycle
+    int m;                // restart length (leading dimension of H is m+1)
+    int record;           // write the residual history
+    long long iters;      // Arnoldi steps so far (all cycles)
+    long long reorths;
+    double bnorm, target; // ||b||, tau ||b||
+    double beta, rinf;    // ||r0||_2, ||r0||_inf of the current cycle
+    double omega;         // ||A z|| of the current step (Fig. 1 step 4)
+    double eps_bd;        // breakdown threshold
+    double est;           // |g_{j+1}|
+    double hn;            // h_{j+1,j}
+    long long hist_cap;
+    int last_k;           // columns of the previous cycle (set when a cycle starts)
+    int pad0;
+};
+
+// per-handle arrays addressed by the kernels
+struct DevArrays {
+    DevState* st;
+    double* H;            // (m+1) x m raw Hessenberg, column-major
+    double* R;            // rotated copy
+    double* cs;           // Givens cosines [m]
+    double* sn;           // Givens sines   [m]
+    double* g;            // rhs of the least-squares problem [m+1]
+    double* y;            // solution [m+1] (zero beyond k)
+    double* h;            // CGS coefficients, pass 1 [m+1]
+    double* u;            // CGS coefficients, pass 2 [m+1]
+    double* scales;       // decode scale per basis column [m+1]
+    double* hist;         // recurrence residual history (device)
+    double* part;         // per-block partial sums [gridmax * (m+2)]
+    double* part_norm;    // per-block (sum of squares, max) of the axpy epilogue [gridmax*2]
+    double* part_spmv;    // per-block sum of squares and max of SpMV / residual [gridmax*2]
+    unsigned int* counters;   // last-block counters (zeroed, reset by the last block)
+    int* flag_host;       // mapped host copy of `active` (may be null)
+};
+
+// ============================================================================ helpers
+__device__ __forceinline__ bool last_block(unsigned int* counter)
+{
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int prev = atomicAdd(counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        if (threadIdx.x == 0) *counter = 0u;   // ready for the next launch
+    }
+    return is_last;
+}
+
+// FP64 value of element e of a decoded chunk (scale not applied); exact for every format
+template <int FMT>
+__device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& ch, int e)
+{
+    if constexpr (FMT == F64) {
+        const unsigned int w[4] = {raw.x, raw.y, raw.z, raw.w};
+        return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
+    } else if constexpr (SingleFloat<FMT>::value) {
+        return (double)ch.vh[e];
+    } else {
+        return __dadd_rn((double)ch.vh[e], (double)ch.vl[e]);
+    }
+}
+
+// padded shared-memory index of row r of a staged w tile (conflict-free 16-B reads by
+// four row subgroups of a warp)
+template <int E> __device__ __forceinline__ int ws_idx(int r) { return r + 2 * (r / E); }
+
+// ============================================================== h = V^T w  (steps 5, 8)
+// Lane-per-column schedule: lane l of a warp owns column cg*8 + (l & 7) and row
+// subgroup l >> 3; its 16-byte loads walk down that column, w comes from shared memory
+// as a broadcast, and the partial sum for the column stays in the lane's registers
+// until the block ends.  No per-column reduction inside the hot loop.
+struct DotArgs {
+    const unsigned char* V;
+    long long ldb;            // bytes per column
+    int ncols;
+    const int* ncols_dev;     // if non-null, read ncols from device (columns k..)
+    const double* scales;
+    const double* w;          // FP64 vector, ld elements
+    long long nrows;          // ld (multiple of DOT_TR)
+    double* part;             // [gridDim.x][MAXCOLS]
+    unsigned int* counter;
+    double* out;              // [ncols]
+    const int* active;        // skip when *active == 0 (may be null)
+};
+
+template <int FMT, int ARITH>
+__global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
+{
+    if (a.active && *a.active == 0) return;
+    constexpr int BS = FmtInfo<FMT>::bytes;
+    constexpr int E = 16 / BS;
+    constexpr int STEPS = DOT_TR / (4 * E);
+    constexpr int MAXP = 4;                        // pairs per warp (MAXCOLS/8/8)
+    __shared__ __align__(16) float2 ws[DOT_TR + 2 * (DOT_TR / E)];
+    const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncg = (ncols + 7) >> 3;
+    const int nph = ncg >= 8 ? 1 : 8 / ncg;
+    const int npairs = ncg * nph;
+    const int sub = lane >> 3;
+
+    float aS[MAXP], aC[MAXP];
+    double aD[MAXP];
+#pragma unroll
+    for (int p = 0; p < MAXP; p++) { aS[p] = 0.f; aC[p] = 0.f; aD[p] = 0.0; }
+
+    const long long ntiles = a.nrows / DOT_TR;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long r0 = t * DOT_TR;
+        __syncthreads();
+        for (int r = threadIdx.x; r < DOT_TR; r += THREADS) {
+            double wv = a.w[r0 + r];
+            float2 s;
+            if constexpr (ARITH == ARITH_DF32) split_f64(wv, s.x, s.y);
+            else s = *reinterpret_cast<float2*>(&wv);
+            ws[ws_idx<E>(r)] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int pi = 0; pi < MAXP; pi++) {
+            const int p = warp + 8 * pi;
+            if (p >= npairs) break;
+            const int cg = p % ncg, ph = p / ncg;
+            const int col = cg * 8 + (lane & 7);
+            if (col >= ncols) continue;
+            const unsigned char* cp = a.V + (long long)col * a.ldb + r0 * BS;
+            float S = 0.f, C = 0.f;
+            double D = 0.0;
+#pragma unroll 4
+            for (int s = ph; s < STEPS; s += nph) {
+                const int row = s * 4 * E + sub * E;
+                uint4 raw = ldg_stream(cp + (long long)row * BS);
+                Chunk<FMT> ch;
+                decode_chunk<FMT>(raw, ch);
+                const float2* wp = ws + ws_idx<E>(row);
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    float2 wv = wp[e];
+                    if constexpr (ARITH == ARITH_DF32) {
+                        if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
+                        else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
+                    } else {
+                        double wd = *reinterpret_cast<const double*>(&wv);
+                        D = __fma_rn(chunk_f64<FMT>(raw, ch, e), wd, D);
+                    }
+                }
+                if constexpr (ARITH == ARITH_DF32) df_renorm(S, C);
+            }
+            if constexpr (ARITH == ARITH_DF32) df_add(aS[pi], aC[pi], S, C);
+            else aD[pi] += D;
+        }
+    }
+
+    // ---- block reduction: red[p][lane] -> per column, then across blocks
+    __syncthreads();
+    float2* red = ws;   // reuse (needs npairs*32 <= DOT_TR entries: npairs <= 32)
+#pragma unroll
+    for (int pi = 0; pi < MAXP; pi++) {
+        const int p = warp + 8 * pi;
+        if (p < npairs) {
+            float2 v;
+            if constexpr (ARITH == ARITH_DF32) v = make_float2(aS[pi], aC[pi]);
+            else v = *reinterpret_cast<float2*>(&aD[pi]);
+            red[p * 32 + lane] = v;
+        }
+    }
+    __syncthreads();
+    for (int col = threadIdx.x; col < ncols; col += THREADS) {
+        const int cg = col >> 3, c8 = col & 7;
+        double tot;
+        if constexpr (ARITH == ARITH_DF32) {
+            float S = 0.f, C = 0.f;
+            for (int ph = 0; ph < nph; ph++)
+                for (int sb = 0; sb < 4; sb++) {
+                    float2 v = red[(ph * ncg + cg) * 32 + sb * 8 + c8];
+                    df_add(S, C, v.x, v.y);
+                }
+            tot = df_to_double(S, C);
+        } else {
+            tot = 0.0;
+            for (int ph = 0; ph < nph; ph++)
+                for (int sb = 0; sb < 4; sb++) {
+                    float2 v = red[(ph * ncg + cg) * 32 + sb * 8 + c8];
+                    tot += *reinterpret_cast<double*>(&v);
+                }
+        }
+        a.part[(long long)blockIdx.x * MAXCOLS + col] = tot;
+    }
+    if (last_block(a.counter)) {
+        for (int col = threadIdx.x; col < ncols; col += THREADS) {
+            double s = 0.0;
+            for (unsigned int b = 0; b < gridDim.x; b++) s += __ldcg(a.part + (long long)b * MAXCOLS + col);
+            a.out[col] = s * a.scales[col];
+        }
+    }
+}
+
+// ====================================================== w_out = w_in + sum_k V_k c_k
+// c_k = sign * scales[k] * coef[k].  Row-per-thread schedule: each thread owns E
+// consecutive rows, reads 16 B of every column (coalesced across the warp) and keeps E
+// double-float accumulators.  Epilogue modes:
+//   EPI_SUB   w_out = w_in - V coef, plus per-block sum of squares and max |w_out|
+//   EPI_XUPD  x += dinv .* (V coef) (dinv may be null), x = w_out, w_in unused
+//   EPI_PLAIN w_out = V coef
+constexpr int EPI_SUB = 0, EPI_XUPD = 1, EPI_PLAIN = 2;
+
+struct AxpyArgs {
+    const unsigned char* V;
+    long long ldb;
+    int ncols;
+    const int* ncols_dev;
+    const double* scales;
+    const double* coef;       // device [ncols]
+    double sign;
+    const double* w_in;
+    double* w_out;
+    const double* dinv;       // Jacobi (EPI_XUPD), may be null
+    long long nrows;          // ld
+    long long n;              // true rows (norms exclude padding)
+    double* part_norm;        // [gridDim.x][2]
+    const int* active;
+};
+
+template <int FMT, int ARITH, int EPI>
+__global__ void __launch_bounds__(THREADS) k_basis_axpy(AxpyArgs a)
+{
+    if (a.active && *a.active == 0) return;
+    constexpr int BS = FmtInfo<FMT>::bytes;
+    constexpr int E = 16 / BS;
+    __shared__ float2 cs[MAXCOLS];
+    __shared__ double red_s[THREADS / 32], red_m[THREADS / 32];
+    const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
+    for (int k = threadIdx.x; k < ncols; k += THREADS) {
+        double c = a.sign * a.scales[k] * a.coef[k];
+        float2 s;
+        if constexpr (ARITH == ARITH_DF32) split_f64(c, s.x, s.y);
+        else s = *reinterpret_cast<float2*>(&c);
+        cs[k] = s;
+    }
+    __syncthreads();
+
+    double ss = 0.0;             // epilogue partials: sum of squares (FP64) and
+    unsigned long long mxb = 0;  // max |w| as the bit pattern of a non-negative double
+    const long long rows_per_block = (long long)THREADS * E;
+    const long long nblk = a.nrows / rows_per_block;
+    for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const long long row0 = b * rows_per_block + (long long)threadIdx.x * E;
+        const unsigned char* base = a.V + row0 * BS;
+        float S[E], C[E];
+        double D[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) { S[e] = 0.f; C[e] = 0.f; D[e] = 0.0; }
+        int k = 0;
+        for (; k + 4 <= ncols; k += 4) {
+            uint4 raw[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                Chunk<FMT> ch;
+                decode_chunk<FMT>(raw[q], ch);
+                float2 c = cs[k + q];
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    if constexpr (ARITH == ARITH_DF32) {
+                        if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
+                        else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
+                    } else {
+                        double cd = *reinterpret_cast<double*>(&c);
+                        D[e] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), cd, D[e]);
+                    }
+                }
+            }
+            if constexpr (ARITH == ARITH_DF32) {
+#pragma unroll
+                for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+            }
+        }
+        for (; k < ncols; k++) {
+            uint4 raw = ldg_stream(base + (long long)k * a.ldb);
+            Chunk<FMT> ch;
+            decode_chunk<FMT>(raw, ch);
+            float2 c = cs[k];
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if constexpr (ARITH == ARITH_DF32) {
+                    if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
+                    else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
+                } else {
+                    double cd = *reinterpret_cast<double*>(&c);
+                    D[e] = __fma_rn(chunk_f64<FMT>(raw, ch, e), cd, D[e]);
+                }
+            }
+        }
+        // epilogue
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const long long i = row0 + e;
+            double acc;
+            if constexpr (ARITH == ARITH_DF32) {
+                if constexpr (EPI == EPI_SUB) {
+                    float wh, wl;
+                    split_f64(a.w_in[i], wh, wl);
+                    df_add(S[e], C[e], wh, wl);
+                }
+                acc = df_to_double(S[e], C[e]);
+            } else {
+                acc = D[e];
+                if constexpr (EPI == EPI_SUB) acc = __dadd_rn(a.w_in[i], acc);
+            }
+            if constexpr (EPI == EPI_SUB) {
+                a.w_out[i] = acc;
+                if (i < a.n) {
+                    ss = __fma_rn(acc, acc, ss);
+                    unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & 0x7FFFFFFFFFFFFFFFull;
+                    mxb = ab > mxb ? ab : mxb;
+                }
+            } else if constexpr (EPI == EPI_XUPD) {
+                if (i < a.n) {
+                    double d = a.dinv ? __dmul_rn(a.dinv[i], acc) : acc;
+                    a.w_out[i] = __dadd_rn(a.w_out[i], d);
+                }
+            } else {
+                a.w_out[i] = acc;
+            }
+        }
+    }
+    if constexpr (EPI == EPI_SUB) {
+        ss = warp_sum(ss);
+        double mx = warp_max(__longlong_as_double((long long)mxb));
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0, m = 0.0;
+            for (int w = 0; w < THREADS / 32; w++) { s += red_s[w]; m = fmax(m, red_m[w]); }
+            a.part_norm[2 * blockIdx.x] = s;
+            a.part_norm[2 * blockIdx.x + 1] = m;
+        }
+    }
+}
+
+// ========================================== store v_{j+1} = w / h_{j+1,j} (steps 6, 12-14)
+// Every block reduces the per-block norm partials of the preceding axpy (cheap and
+// deterministic), forms h_{j+1,j}, 1/h and max|v|, and encodes its rows into column
+// `col`.  Block 0 additionally completes the Hessenberg column j (h from pass 1 plus u
+// from pass 2), applies the Givens rotations (Section 2), updates g, writes the
+// residual history and decides whether the cycle continues.
+// mode 0: Arnoldi step (finalize + store column j+1); mode 1: first vector of a cycle
+// (w = r0, norms from the residual kernel, no Hessenberg work).
+struct StoreArgs {
+    DevArrays d;
+    const double* w;
+    unsigned char* Vcol;      // destination column
+    int col;                  // index of the destination column (scale slot)
+    int j;                    // Hessenberg column being completed (mode 0)
+    int mode;
+    int reorth;               // pass 2 ran (h += u)
+    const double* part_norm;  // per-block (sumsq, max) from the producer
+    int nparts;
+    long long n;
+    int fmt;
+};
+
+__device__ __forceinline__ void reduce_norm_parts(const double* part, int np, double& ss, double& mx)
+{
+    // fixed order: lane l sums parts l, l+32, ...; then a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    double s = 0.0, m = 0.0;
+    for (int p = lane; p < np; p += 32) { s += __ldcg(part + 2 * p); m = fmax(m, __ldcg(part + 2 * p + 1)); }
+    ss = warp_sum(s);
+    mx = warp_max(m);
+}
+
+static __device__ void arnoldi_finalize(const StoreArgs& a, double hn)
+{
+    // executed by thread 0 of block 0
+    DevState* st = a.d.st;
+    const int j = a.j, ldh = st->m + 1;
+    double* Hc = a.d.H + (long long)j * ldh;
+    double* Rc = a.d.R + (long long)j * ldh;
+    for (int i = 0; i <= j; i++) {
+        double hv = __ldcg(a.d.h + i);
+        if (a.reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
+        Hc[i] = hv;
+        Rc[i] = hv;
+    }
+    Hc[j + 1] = hn;
+    Rc[j + 1] = hn;
+    for (int i = j + 2; i < ldh; i++) { Hc[i] = 0.0; Rc[i] = 0.0; }
+    for (int i = 0; i < j; i++) {
+        double c = a.d.cs[i], s = a.d.sn[i];
+        double t0 = __dadd_rn(__dmul_rn(c, Rc[i]), __dmul_rn(s, Rc[i + 1]));
+        double t1 = __dadd_rn(__dmul_rn(-s, Rc[i]), __dmul_rn(c, Rc[i + 1]));
+        Rc[i] = t0;
+        Rc[i + 1] = t1;
+    }
+    double rr = hypot(Rc[j], Rc[j + 1]);
+    double c, s;
+    if (rr == 0.0) { c = 1.0; s = 0.0; }
+    else { c = Rc[j] / rr; s = Rc[j + 1] / rr; }
+    a.d.cs[j] = c;
+    a.d.sn[j] = s;
+    Rc[j] = rr;
+    Rc[j + 1] = 0.0;
+    double gj = a.d.g[j];
+    a.d.g[j + 1] = __dmul_rn(-s, gj);
+    a.d.g[j] = __dmul_rn(c, gj);
+    double est = fabs(a.d.g[j + 1]);
+    st->est = est;
+    st->hn = hn;
+    st->k = j + 1;
+    st->iters += 1;
+    if (a.reorth) st->reorths += 1;
+    if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
+    int stop = 0;
+    if (!isfinite(hn) || !isfinite(st->omega) || !isfinite(est)) stop = 3;
+    else if (!(hn > st->eps_bd * st->omega)) stop = 2;
+    else if (est <= st->target) stop = 1;
+    else if (j + 1 >= st->kcap) stop = 4;
+    if (stop) {
+        st->stop = stop;
+        st->active = 0;
+        if (a.d.flag_host) *(volatile int*)a.d.flag_host = 0;
+    }
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
+{
+    DevState* st = a.d.st;
+    if (st->active == 0) return;
+    __shared__ double sh_inv, sh_hn;
+    __shared__ EncParams sh_ep;
+    if (threadIdx.x < 32) {
+        double ss, mx;
+        reduce_norm_parts(a.part_norm, a.nparts, ss, mx);
+        if (threadIdx.x == 0) {
+            double hn = sqrt(ss);
+            if (a.mode == 1) {           // first vector: norms of r0 from the residual kernel
+                hn = st->beta;
+                mx = st->rinf;
+            }
+            double inv = 1.0 / hn;
+            sh_hn = hn;
+            sh_inv = inv;
+            sh_ep = enc_params(FMT, __dmul_rn(mx, inv));
+        }
+    }
+    __syncthreads();
+    const double inv = sh_inv;
+    const EncParams ep = sh_ep;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.d.scales[a.col] = ep.scale;
+        if (a.mode == 0) arnoldi_finalize(a, sh_hn);
+    }
+    const long long stride = (long long)gridDim.x * THREADS;
+    for (long long i = (long long)blockIdx.x * THREADS + threadIdx.x; i < a.n; i += stride) {
+        double v = __dmul_rn(a.w[i], inv);
+        encode_store<FMT>(a.Vcol, i, v, ep);
+    }
+}
+
+// ======================================================= SpMV with on-the-fly decode
+// y = A x (x FP64) or y = A dec(code column) (Fig. 1 step 3; right preconditioning with
+// Jacobi is folded into the stored values A D^{-1}).  GROUP lanes per CSR row.  The
+// per-block sum of squares and max |y| of the owned rows go to part; in residual mode
+// y = b - A x.  The last block turns the partials into omega (Arnoldi mode) or beta /
+// ||r||_inf and the cycle's active flag (residual mode).
+constexpr int SPMV_ARNOLDI = 0, SPMV_RESIDUAL = 1, SPMV_PLAIN = 2, SPMV_ACCUM = 3;
+
+struct SpmvArgs {
+    const int* rowptr;
+    const int* col;
+    const double* val;
+    const void* x;            // FP64 vector or code column
+    double xscale;
+    const double* xscale_dev; // per-column scale on device (Arnoldi mode)
+    const double* b;          // residual mode
+    double* y;
+    long long n;
+    double* part;             // [gridDim.x][2]
+    unsigned int* counter;
+    DevState* st;             // Arnoldi: omega; residual: beta, rinf, active
+    int* flag_host;
+    const int* active;
+};
+
+template <int XFMT, int GROUP, int MODE>
+__global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
+{
+    if (MODE == SPMV_ARNOLDI && a.active && *a.active == 0) return;
+    __shared__ double red_s[THREADS / 32], red_m[THREADS / 32];
+    const int lane_g = threadIdx.x & (GROUP - 1);
+    const long long gid = ((long long)blockIdx.x * THREADS + threadIdx.x) / GROUP;
+    const long long ngroups = (long long)gridDim.x * THREADS / GROUP;
+    const double xs = a.xscale_dev ? *a.xscale_dev : a.xscale;
+    double ss = 0.0, mx = 0.0;
+    for (long long row = gid;; row += ngroups) {
+        const bool valid = row < a.n;
+        if constexpr (GROUP > 1) {
+            if (__all_sync(0xFFFFFFFFu, !valid)) break;   // warp-uniform exit around shuffles
+        } else {
+            if (!valid) break;
+        }
+        const int p0 = valid ? a.rowptr[row] : 0, p1 = valid ? a.rowptr[row + 1] : 0;
+        double s = 0.0;
+        for (int p = p0 + lane_g; p < p1; p += GROUP) {
+            const int c = a.col[p];
+            double xv;
+            if constexpr (XFMT < 0) xv = reinterpret_cast<const double*>(a.x)[c];
+            else xv = code_value<XFMT>(a.x, c);
+            s = __fma_rn(a.val[p], xv, s);
+        }
+        if constexpr (GROUP > 1) {
+#pragma unroll
+            for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        }
+        if constexpr (XFMT >= 0) s = __dmul_rn(s, xs);
+        if (valid && lane_g == 0) {
+            double yv = s;
+            if constexpr (MODE == SPMV_RESIDUAL) yv = __dsub_rn(a.b[row], s);
+            if constexpr (MODE == SPMV_ACCUM) yv = __dadd_rn(a.y[row], s);
+            a.y[row] = yv;
+            ss = __fma_rn(yv, yv, ss);
+            mx = fmax(mx, fabs(yv));
+        }
+    }
+    if constexpr (MODE == SPMV_PLAIN || MODE == SPMV_ACCUM) return;
+    else {
+        ss = warp_sum(ss);
+        mx = warp_max(mx);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0, m = 0.0;
+            for (int w = 0; w < THREADS / 32; w++) { s += red_s[w]; m = fmax(m, red_m[w]); }
+            a.part[2 * blockIdx.x] = s;
+            a.part[2 * blockIdx.x + 1] = m;
+        }
+        if (last_block(a.counter)) {
+            if (threadIdx.x < 32) {
+                double s2, m2;
+                reduce_norm_parts(a.part, gridDim.x, s2, m2);
+                if (threadIdx.x == 0) {
+                    DevState* st = a.st;
+                    if (MODE == SPMV_ARNOLDI) {
+                        st->omega = sqrt(s2);
+                    } else {
+                        st->beta = sqrt(s2);
+                        st->rinf = m2;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ================================================================ codec test kernels
+template <int FMT>
+__global__ void k_encode_vec(const double* v, long long n, unsigned char* codes, EncParams ep)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        encode_store<FMT>(codes, i, v[i], ep);
+}
+
+template <int FMT>
+__global__ void k_decode_vec(const unsigned char* codes, long long n, double scale, double* out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __dmul_rn(code_value<FMT>(codes, i), scale);
+}
+
+}  // namespace cbg

@@ -1,0 +1,28 @@
+// cbg_launch.h -- declarations of the host-side kernel launchers.  The definitions live
+// in cbg_launch_impl.cuh and are instantiated once per basis format (basis_<fmt>.cu), so
+// the seven formats compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cbg_kernels.cuh"
+
+namespace cbg {
+
+template <int FMT> struct Launcher {
+    static void dot(int arith, int grid, cudaStream_t s, const DotArgs& a);
+    static void axpy(int arith, int epi, int grid, cudaStream_t s, const AxpyArgs& a);
+    static void store(int grid, cudaStream_t s, const StoreArgs& a);
+    static void spmv_code(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a);
+    static void encode(int grid, cudaStream_t s, const double* v, long long n, unsigned char* codes,
+                       EncParams ep);
+    static void decode(int grid, cudaStream_t s, const unsigned char* codes, long long n, double scale,
+                       double* out);
+    static int occupancy_dot();
+    static int occupancy_axpy();
+};
+
+// SpMV with an FP64 input vector (residual, SPAI second stage, x += P t)
+void spmv_f64(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a);
+int spmv_occupancy();
+
+}  // namespace cbg

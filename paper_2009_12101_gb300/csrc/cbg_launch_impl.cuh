@@ -1,0 +1,77 @@
+// cbg_launch_impl.cuh -- definitions of the launchers declared in cbg_launch.h.
+#pragma once
+#include "cbg_launch.h"
+
+namespace cbg {
+
+#define CBG_SPMV_GROUPS(XF, MODE)                                                              \
+    switch (group) {                                                                           \
+    case 1: k_spmv<XF, 1, MODE><<<grid, THREADS, 0, s>>>(a); break;                            \
+    case 2: k_spmv<XF, 2, MODE><<<grid, THREADS, 0, s>>>(a); break;                            \
+    case 4: k_spmv<XF, 4, MODE><<<grid, THREADS, 0, s>>>(a); break;                            \
+    case 8: k_spmv<XF, 8, MODE><<<grid, THREADS, 0, s>>>(a); break;                            \
+    case 16: k_spmv<XF, 16, MODE><<<grid, THREADS, 0, s>>>(a); break;                          \
+    default: k_spmv<XF, 32, MODE><<<grid, THREADS, 0, s>>>(a); break;                          \
+    }
+
+template <int FMT> void Launcher<FMT>::dot(int arith, int grid, cudaStream_t s, const DotArgs& a)
+{
+    if (arith == ARITH_DF32) k_basis_dot<FMT, ARITH_DF32><<<grid, THREADS, 0, s>>>(a);
+    else k_basis_dot<FMT, ARITH_FP64><<<grid, THREADS, 0, s>>>(a);
+}
+
+template <int FMT>
+void Launcher<FMT>::axpy(int arith, int epi, int grid, cudaStream_t s, const AxpyArgs& a)
+{
+    if (arith == ARITH_DF32) {
+        if (epi == EPI_SUB) k_basis_axpy<FMT, ARITH_DF32, EPI_SUB><<<grid, THREADS, 0, s>>>(a);
+        else if (epi == EPI_XUPD) k_basis_axpy<FMT, ARITH_DF32, EPI_XUPD><<<grid, THREADS, 0, s>>>(a);
+        else k_basis_axpy<FMT, ARITH_DF32, EPI_PLAIN><<<grid, THREADS, 0, s>>>(a);
+    } else {
+        if (epi == EPI_SUB) k_basis_axpy<FMT, ARITH_FP64, EPI_SUB><<<grid, THREADS, 0, s>>>(a);
+        else if (epi == EPI_XUPD) k_basis_axpy<FMT, ARITH_FP64, EPI_XUPD><<<grid, THREADS, 0, s>>>(a);
+        else k_basis_axpy<FMT, ARITH_FP64, EPI_PLAIN><<<grid, THREADS, 0, s>>>(a);
+    }
+}
+
+template <int FMT> void Launcher<FMT>::store(int grid, cudaStream_t s, const StoreArgs& a)
+{
+    k_store<FMT><<<grid, THREADS, 0, s>>>(a);
+}
+
+template <int FMT>
+void Launcher<FMT>::spmv_code(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a)
+{
+    if (mode == SPMV_ARNOLDI) { CBG_SPMV_GROUPS(FMT, SPMV_ARNOLDI) }
+    else { CBG_SPMV_GROUPS(FMT, SPMV_PLAIN) }
+}
+
+template <int FMT>
+void Launcher<FMT>::encode(int grid, cudaStream_t s, const double* v, long long n, unsigned char* codes,
+                           EncParams ep)
+{
+    k_encode_vec<FMT><<<grid, THREADS, 0, s>>>(v, n, codes, ep);
+}
+
+template <int FMT>
+void Launcher<FMT>::decode(int grid, cudaStream_t s, const unsigned char* codes, long long n, double scale,
+                           double* out)
+{
+    k_decode_vec<FMT><<<grid, THREADS, 0, s>>>(codes, n, scale, out);
+}
+
+template <int FMT> int Launcher<FMT>::occupancy_dot()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_basis_dot<FMT, ARITH_DF32>, THREADS, 0);
+    return b;
+}
+
+template <int FMT> int Launcher<FMT>::occupancy_axpy()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_basis_axpy<FMT, ARITH_DF32, EPI_SUB>, THREADS, 0);
+    return b;
+}
+
+}  // namespace cbg

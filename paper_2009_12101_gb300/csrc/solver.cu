@@ -1,0 +1,944 @@
+// solver.cu -- host driver of the restarted Arnoldi process and the C ABI (cbgmres.h).
+//
+// One restart cycle (Fig. 1):
+//   residual kernel     r = b - A x, beta = ||r||, ||r||_inf        (step 1 / step 18)
+//   cycle-start kernel  decides whether the cycle runs, g = beta e1
+//   store (mode 1)      v_1 = r / beta, compressed into V[:,0]
+//   per step j (all enqueued asynchronously, self-disabling once the cycle stops):
+//     spmv     w = A M^{-1} v_j  (decode fused), omega = ||w||       (steps 3-4)
+//     dot      h = V_j^T w                                           (step 5)
+//     axpy     w1 = w - V_j h                                        (step 5)
+//     dot      u = V_j^T w1                                          (step 8)
+//     axpy     w2 = w1 - V_j u, ||w2||_2, ||w2||_inf                 (steps 8-10)
+//     store    h_{j+1,j} = ||w2||, Givens update, v_{j+1} -> V        (steps 6, 12-14)
+//   backsolve y = R^{-1} g; x += M^{-1} (V y)                        (step 17)
+// The host reads the explicit residual once per cycle and polls a mapped flag every
+// `check_every` steps to stop enqueueing once the device has ended the cycle.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cbgmres.h"
+#include "cbg_launch.h"
+
+using namespace cbg;
+
+namespace {
+
+#define CBG_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            last_cuda_error = e_;                        \
+            return CBG_ERR_CUDA;                         \
+        }                                                \
+    } while (0)
+
+thread_local cudaError_t last_cuda_error = cudaSuccess;
+
+int fmt_bytes(int fmt)
+{
+    switch (fmt) {
+    case CBG_F64: return 8;
+    case CBG_F32: case CBG_I32: return 4;
+    case CBG_F16: case CBG_BF16: case CBG_I16: return 2;
+    case CBG_E4M3: return 1;
+    default: return 0;
+    }
+}
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// ------------------------------------------------------------------ format dispatch
+struct Ops {
+    void (*dot)(int, int, cudaStream_t, const DotArgs&);
+    void (*axpy)(int, int, int, cudaStream_t, const AxpyArgs&);
+    void (*store)(int, cudaStream_t, const StoreArgs&);
+    void (*spmv_code)(int, int, int, cudaStream_t, const SpmvArgs&);
+    void (*encode)(int, cudaStream_t, const double*, long long, unsigned char*, EncParams);
+    void (*decode)(int, cudaStream_t, const unsigned char*, long long, double, double*);
+    int (*occ_dot)();
+    int (*occ_axpy)();
+};
+
+template <int F> Ops make_ops()
+{
+    return Ops{&Launcher<F>::dot, &Launcher<F>::axpy, &Launcher<F>::store, &Launcher<F>::spmv_code,
+               &Launcher<F>::encode, &Launcher<F>::decode, &Launcher<F>::occupancy_dot,
+               &Launcher<F>::occupancy_axpy};
+}
+
+const Ops& ops_for(int fmt)
+{
+    static const Ops table[7] = {make_ops<F64>(), make_ops<F32>(), make_ops<F16>(), make_ops<BF16>(),
+                                 make_ops<E4M3>(), make_ops<I32>(), make_ops<I16>()};
+    return table[fmt];
+}
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+// --------------------------------------------------------------- small helper kernels
+__global__ void k_jacobi_prepare(const int* rowptr, const int* col, const double* val, long long n,
+                                 double* dinv, int* bad)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (col[p] == i) d = val[p];
+        if (d == 0.0 || !isfinite(d)) { atomicExch(bad, 1); dinv[i] = 0.0; }
+        else dinv[i] = 1.0 / d;
+    }
+}
+
+__global__ void k_scale_columns(const int* col, const double* val, const double* dinv, long long nnz, double* out)
+{
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x)
+        out[p] = __dmul_rn(val[p], dinv[col[p]]);
+}
+
+// ||v||_2 and finiteness of a vector; one block, fixed reduction order
+__global__ void k_norm_check(const double* v, long long n, double* out /* [2]: norm, finite */)
+{
+    __shared__ double red[THREADS / 32];
+    __shared__ int fin;
+    if (threadIdx.x == 0) fin = 1;
+    __syncthreads();
+    double s = 0.0;
+    int ok = 1;
+    for (long long i = threadIdx.x; i < n; i += THREADS) {
+        double x = v[i];
+        if (!isfinite(x)) ok = 0;
+        s = __fma_rn(x, x, s);
+    }
+    if (!ok) fin = 0;
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < THREADS / 32; w++) t += red[w];
+        out[0] = sqrt(t);
+        out[1] = fin;
+    }
+}
+
+__global__ void k_init_state(DevState* st, double bnorm, double target, double eps_bd, int m, int record,
+                             long long hist_cap)
+{
+    st->active = 0;
+    st->k = 0;
+    st->stop = 0;
+    st->kcap = 0;
+    st->m = m;
+    st->record = record;
+    st->iters = 0;
+    st->reorths = 0;
+    st->bnorm = bnorm;
+    st->target = target;
+    st->beta = 0.0;
+    st->rinf = 0.0;
+    st->omega = 0.0;
+    st->eps_bd = eps_bd;
+    st->est = 0.0;
+    st->hn = 0.0;
+    st->hist_cap = hist_cap;
+    st->last_k = 0;
+}
+
+// ================================================ cycle start / end (single block)
+// start: decide whether a new cycle runs, reset g, counters of the cycle.
+__global__ void k_cycle_start(DevArrays d, long long maxit, int m)
+{
+    if (threadIdx.x != 0) return;
+    DevState* st = d.st;
+    const double beta = st->beta;
+    int run = beta > st->target && st->iters < maxit && isfinite(beta);
+    long long left = maxit - st->iters;
+    st->kcap = (int)(left < m ? left : m);
+    st->last_k = st->k;
+    st->k = 0;
+    st->stop = 0;
+    st->active = run;
+    if (d.flag_host) *(volatile int*)d.flag_host = run;
+    for (int i = 0; i <= m; i++) { d.g[i] = 0.0; d.y[i] = 0.0; }
+    d.g[0] = beta;
+}
+
+// y = R^{-1} g on the k x k upper triangle (Fig. 1 step 17); one warp.
+__global__ void k_backsolve(DevArrays d)
+{
+    DevState* st = d.st;
+    const int k = st->k, ldh = st->m + 1;
+    const int lane = threadIdx.x;
+    for (int i = k - 1; i >= 0; i--) {
+        double s = 0.0;
+        for (int c = i + 1 + lane; c < k; c += 32) s = __fma_rn(d.R[i + (long long)c * ldh], d.y[c], s);
+        s = warp_sum(s);
+        if (lane == 0) d.y[i] = (d.g[i] - s) / d.R[i + (long long)i * ldh];
+        __syncwarp();
+    }
+    for (int i = k + lane; i <= st->m; i += 32) d.y[i] = 0.0;
+}
+
+}  // namespace
+
+// ======================================================================== the handle
+struct cbg_handle {
+    long long n = 0, nnz = 0, ld = 0, ldb = 0;
+    int m = 0, fmt = 0;
+    cbg_options opt{};
+    cudaStream_t stream = nullptr;
+    // matrix
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;     // A
+    double* valp = nullptr;    // A D^{-1} (Jacobi) or nullptr
+    double* dinv = nullptr;    // D^{-1}
+    double* pvals = nullptr;   // SPAI values (A's pattern)
+    // basis and vectors
+    unsigned char* V = nullptr;
+    double *w = nullptr, *w1 = nullptr, *w2 = nullptr, *r = nullptr, *tmp = nullptr, *z = nullptr;
+    double *bdev = nullptr, *xdev = nullptr;   // staging for cbgmres_solve_host
+    double* scratch = nullptr;                 // small reductions
+    // solver state
+    DevArrays d{};
+    void* state_block = nullptr;
+    int* flag_host = nullptr;
+    int* flag_dev = nullptr;
+    long long hist_alloc = 0;
+    int grid_dot = 0, grid_axpy = 0, grid_store = 0, grid_spmv = 0, group = 1, gridmax = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> step_ev;
+};
+
+namespace {
+
+void free_handle(cbg_handle* h)
+{
+    if (!h) return;
+    cudaFree(h->rowptr); cudaFree(h->col); cudaFree(h->val); cudaFree(h->valp); cudaFree(h->dinv);
+    cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
+    cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
+    cudaFree(h->state_block); cudaFree(h->d.hist);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto e : h->step_ev) cudaEventDestroy(e);
+    delete h;
+}
+
+int validate_csr_host(long long n, long long nnz, const int* rp, const int* ci)
+{
+    if (rp[0] != 0 || rp[n] != nnz) return CBG_ERR_ARG;
+    for (long long i = 0; i < n; i++)
+        if (rp[i + 1] < rp[i]) return CBG_ERR_ARG;
+    for (long long p = 0; p < nnz; p++)
+        if (ci[p] < 0 || ci[p] >= n) return CBG_ERR_ARG;
+    return CBG_OK;
+}
+
+template <class T> int dalloc(T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        last_cuda_error = e;
+        return e == cudaErrorMemoryAllocation ? CBG_ERR_OOM : CBG_ERR_CUDA;
+    }
+    return CBG_OK;
+}
+
+int pick_group(long long n, long long nnz)
+{
+    double mean = n > 0 ? (double)nnz / (double)n : 1.0;
+    if (mean < 10) return 1;
+    if (mean < 20) return 4;
+    if (mean < 48) return 8;
+    if (mean < 96) return 16;
+    return 32;
+}
+
+// ------------------------------------------------------------------ launches per step
+SpmvArgs spmv_args(cbg_handle* h)
+{
+    SpmvArgs a{};
+    a.rowptr = h->rowptr;
+    a.col = h->col;
+    a.n = h->n;
+    a.part = h->d.part_spmv;
+    a.st = h->d.st;
+    return a;
+}
+
+void enqueue_residual(cbg_handle* h, const double* b, const double* x)
+{
+    SpmvArgs a = spmv_args(h);
+    a.val = h->val;
+    a.x = x;
+    a.xscale = 1.0;
+    a.b = b;
+    a.y = h->r;
+    a.counter = h->d.counters + 0;
+    spmv_f64(SPMV_RESIDUAL, h->group, h->grid_spmv, h->stream, a);
+}
+
+void enqueue_step(cbg_handle* h, int j)
+{
+    const Ops& op = ops_for(h->fmt);
+    cudaStream_t s = h->stream;
+    const int* active = &h->d.st->active;
+    const unsigned char* Vj = h->V + (long long)j * h->ldb;
+    // steps 3-4: w = A M^{-1} v_j, omega
+    {
+        SpmvArgs a = spmv_args(h);
+        a.active = active;
+        a.xscale_dev = h->d.scales + j;
+        a.x = Vj;
+        if (h->opt.precond == CBG_PC_SPAI) {
+            a.val = h->pvals;
+            a.y = h->z;
+            op.spmv_code(SPMV_PLAIN, h->group, h->grid_spmv, s, a);   // z = P v
+            SpmvArgs b2 = spmv_args(h);
+            b2.active = active;
+            b2.val = h->val;
+            b2.x = h->z;
+            b2.xscale = 1.0;
+            b2.y = h->w;
+            b2.counter = h->d.counters + 1;
+            spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2);     // w = A z
+        } else {
+            a.val = h->valp ? h->valp : h->val;
+            a.y = h->w;
+            a.counter = h->d.counters + 1;
+            op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a);
+        }
+    }
+    const int ncols = j + 1;
+    const bool reorth = h->opt.reorth != CBG_REORTH_NEVER;
+    // step 5: h = V^T w ; w1 = w - V h
+    DotArgs da{};
+    da.V = h->V;
+    da.ldb = h->ldb;
+    da.ncols = ncols;
+    da.scales = h->d.scales;
+    da.nrows = h->ld;
+    da.part = h->d.part;
+    da.active = active;
+    da.w = h->w;
+    da.counter = h->d.counters + 2;
+    da.out = h->d.h;
+    op.dot(h->opt.arith, h->grid_dot, s, da);
+
+    AxpyArgs xa{};
+    xa.V = h->V;
+    xa.ldb = h->ldb;
+    xa.ncols = ncols;
+    xa.scales = h->d.scales;
+    xa.sign = -1.0;
+    xa.nrows = h->ld;
+    xa.n = h->n;
+    xa.part_norm = h->d.part_norm;
+    xa.active = active;
+    xa.coef = h->d.h;
+    xa.w_in = h->w;
+    xa.w_out = reorth ? h->w1 : h->w2;
+    op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa);
+    if (reorth) {
+        // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
+        da.w = h->w1;
+        da.counter = h->d.counters + 3;
+        da.out = h->d.u;
+        op.dot(h->opt.arith, h->grid_dot, s, da);
+        xa.coef = h->d.u;
+        xa.w_in = h->w1;
+        xa.w_out = h->w2;
+        op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa);
+    }
+    // steps 6, 12-14 and the Givens update
+    StoreArgs sa{};
+    sa.d = h->d;
+    sa.w = h->w2;
+    sa.Vcol = h->V + (long long)(j + 1) * h->ldb;
+    sa.col = j + 1;
+    sa.j = j;
+    sa.mode = 0;
+    sa.reorth = reorth ? 1 : 0;
+    sa.part_norm = h->d.part_norm;
+    sa.nparts = h->grid_axpy;
+    sa.n = h->n;
+    sa.fmt = h->fmt;
+    op.store(h->grid_store, s, sa);
+}
+
+void enqueue_first_vector(cbg_handle* h)
+{
+    StoreArgs sa{};
+    sa.d = h->d;
+    sa.w = h->r;
+    sa.Vcol = h->V;
+    sa.col = 0;
+    sa.j = 0;
+    sa.mode = 1;
+    sa.part_norm = h->d.part_spmv;
+    sa.nparts = 0;
+    sa.n = h->n;
+    sa.fmt = h->fmt;
+    ops_for(h->fmt).store(h->grid_store, h->stream, sa);
+}
+
+void enqueue_cycle_end(cbg_handle* h, double* x)
+{
+    cudaStream_t s = h->stream;
+    k_backsolve<<<1, 32, 0, s>>>(h->d);
+    const Ops& op = ops_for(h->fmt);
+    AxpyArgs xa{};
+    xa.V = h->V;
+    xa.ldb = h->ldb;
+    xa.ncols = 0;
+    xa.ncols_dev = &h->d.st->k;
+    xa.scales = h->d.scales;
+    xa.coef = h->d.y;
+    xa.sign = 1.0;
+    xa.nrows = h->ld;
+    xa.n = h->n;
+    if (h->opt.precond == CBG_PC_SPAI) {
+        xa.w_out = h->tmp;
+        op.axpy(h->opt.arith, EPI_PLAIN, h->grid_axpy, s, xa);       // t = V y
+        SpmvArgs a = spmv_args(h);
+        a.val = h->pvals;
+        a.x = h->tmp;
+        a.xscale = 1.0;
+        a.y = x;
+        spmv_f64(SPMV_ACCUM, h->group, h->grid_spmv, s, a);           // x += P t
+    } else {
+        xa.w_out = x;
+        xa.dinv = h->opt.precond == CBG_PC_JACOBI ? h->dinv : nullptr;
+        op.axpy(h->opt.arith, EPI_XUPD, h->grid_axpy, s, xa);        // x += D^{-1} V y
+    }
+}
+
+struct HostState {
+    DevState st;
+};
+
+int read_state(cbg_handle* h, DevState* out)
+{
+    CBG_CUDA(cudaMemcpyAsync(out, h->d.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+// The whole solve; x (device) holds x0 on entry.  k_only > 0: stop after the first
+// cycle with at most k_only steps (Arnoldi parity runs).
+int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long maxit, cbg_stats* stats,
+              int k_only)
+{
+    if (!h || !b || !x || !(tol >= 0.0) || maxit < 0) return CBG_ERR_ARG;
+    cudaStream_t s = h->stream;
+    CBG_CUDA(cudaEventRecord(h->ev0, s));
+    // ||b|| and finiteness of b and x0
+    k_norm_check<<<1, THREADS, 0, s>>>(b, h->n, h->scratch);
+    k_norm_check<<<1, THREADS, 0, s>>>(x, h->n, h->scratch + 2);
+    double nb[4];
+    CBG_CUDA(cudaMemcpyAsync(nb, h->scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CBG_CUDA(cudaStreamSynchronize(s));
+    CBG_CUDA(cudaGetLastError());
+    const double bnorm = nb[0];
+    int status = CBG_OK;
+    long long cycles = 0;
+    double bytes = 0.0;
+    DevState hs{};
+    const long long hist_cap = stats && stats->history && stats->history_cap > 0 ? stats->history_cap : 0;
+    if (nb[1] == 0.0 || nb[3] == 0.0) {
+        status = CBG_ERR_NONFINITE;
+    } else if (bnorm == 0.0) {
+        CBG_CUDA(cudaMemsetAsync(x, 0, h->n * sizeof(double), s));
+    } else {
+        if (hist_cap > h->hist_alloc) {
+            cudaFree(h->d.hist);
+            h->d.hist = nullptr;
+            int rc = dalloc(&h->d.hist, (size_t)hist_cap);
+            if (rc) return rc;
+            h->hist_alloc = hist_cap;
+        }
+        const double target = tol * bnorm;
+        const long long maxit_eff = k_only > 0 ? std::min<long long>(maxit, k_only) : maxit;
+        k_init_state<<<1, 1, 0, s>>>(h->d.st, bnorm, target, h->opt.breakdown_eps, h->m, hist_cap > 0,
+                                     hist_cap);
+        const double spmv_bytes = (double)h->nnz * 12.0 + (double)(h->n + 1) * 4.0 + 16.0 * (double)h->n;
+        const int L = (int)h->step_ev.size();
+        long long iters_before = -1;
+        for (;;) {
+            enqueue_residual(h, b, x);
+            k_cycle_start<<<1, 1, 0, s>>>(h->d, maxit_eff, h->m);
+            int rc = read_state(h, &hs);
+            if (rc) return rc;
+            for (int j = 0; j < hs.last_k; j++)
+                bytes += spmv_bytes + 4.0 * (double)(j + 1) * (double)h->n * (double)fmt_bytes(h->fmt);
+            if (!hs.active) break;
+            if (k_only > 0 && cycles >= 1) break;
+            if (cycles > 0 && hs.iters == iters_before) return CBG_ERR_CUDA;   // no progress: device work failed
+            iters_before = hs.iters;
+            cycles++;
+            enqueue_first_vector(h);
+            const int kcap = hs.kcap;
+            for (int j = 0; j < kcap; j++) {
+                if (j >= L) {
+                    // keep at most L steps in flight; stop enqueueing once the cycle ended
+                    CBG_CUDA(cudaEventSynchronize(h->step_ev[j % L]));
+                    if (*(volatile int*)h->flag_host == 0) break;
+                }
+                enqueue_step(h, j);
+                CBG_CUDA(cudaEventRecord(h->step_ev[j % L], s));
+            }
+            enqueue_cycle_end(h, x);
+            CBG_CUDA(cudaGetLastError());
+        }
+        if (!std::isfinite(hs.beta)) status = CBG_ERR_NONFINITE;
+        else if (hs.beta <= hs.target) status = CBG_OK;
+        else status = CBG_NOT_CONVERGED;
+    }
+    CBG_CUDA(cudaEventRecord(h->ev1, s));
+    CBG_CUDA(cudaEventSynchronize(h->ev1));
+    CBG_CUDA(cudaGetLastError());
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        stats->iters = hs.iters;
+        stats->restarts = cycles;
+        stats->reorths = hs.reorths;
+        stats->true_relres = bnorm > 0 ? hs.beta / bnorm : 0.0;
+        stats->est_relres = bnorm > 0 ? hs.est / bnorm : 0.0;
+        stats->ms_total = ms;
+        stats->bytes_model = bytes;
+        stats->status = status;
+        stats->history_len = 0;
+        if (hist_cap > 0 && bnorm > 0) {
+            long long nh = std::min<long long>(hs.iters, hist_cap);
+            if (nh > 0)
+                CBG_CUDA(cudaMemcpy(stats->history, h->d.hist, nh * sizeof(double), cudaMemcpyDeviceToHost));
+            stats->history_len = nh;
+        }
+    }
+    return status;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+void cbgmres_options_default(cbg_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->reorth = CBG_REORTH_ALWAYS;
+    o->precond = CBG_PC_NONE;
+    o->arith = CBG_ARITH_DF32;
+    o->spmv_group = 0;
+    o->eta = 0.70710678118654752440;
+    o->breakdown_eps = 1.4210854715202004e-14;   // 2^-46
+    o->stream = nullptr;
+    o->check_every = 4;
+    o->use_graph = 0;
+}
+
+const char* cbgmres_status_string(int s)
+{
+    switch (s) {
+    case CBG_OK: return "converged";
+    case CBG_NOT_CONVERGED: return "not converged within maxit";
+    case CBG_ERR_ARG: return "invalid argument";
+    case CBG_ERR_NONFINITE: return "non-finite value";
+    case CBG_ERR_OOM: return "device out of memory";
+    case CBG_ERR_CUDA: return "CUDA error";
+    case CBG_ERR_TIMEOUT: return "device wait timed out";
+    case CBG_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+    }
+}
+
+int cbgmres_format_bytes(int fmt) { return fmt_bytes(fmt); }
+
+int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* opt, cbg_handle** out)
+{
+    if (!out) return CBG_ERR_ARG;
+    *out = nullptr;
+    if (!A || A->n < 1 || A->nnz < 1 || A->n > 0x7FFFFFFFLL || A->nnz > 0x7FFFFFFFLL || restart < 1 ||
+        restart + 1 > MAXCOLS || fmt_bytes(fmt) == 0 || !A->row_ptr || !A->col || !A->val)
+        return CBG_ERR_ARG;
+    cbg_options o;
+    if (opt) o = *opt;
+    else cbgmres_options_default(&o);
+    if (o.arith != CBG_ARITH_DF32 && o.arith != CBG_ARITH_FP64) return CBG_ERR_ARG;
+    if (o.precond < CBG_PC_NONE || o.precond > CBG_PC_SPAI) return CBG_ERR_ARG;
+    if (o.reorth == CBG_REORTH_CONDITIONAL) return CBG_ERR_UNSUPPORTED;
+    if (o.reorth < CBG_REORTH_ALWAYS || o.reorth > CBG_REORTH_NEVER) return CBG_ERR_ARG;
+    if (o.spmv_group != 0 && (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
+        return CBG_ERR_ARG;
+
+    // validate the CSR on the host
+    const long long n = A->n, nnz = A->nnz;
+    std::vector<int> hrp, hci;
+    const int* rp = A->row_ptr;
+    const int* ci = A->col;
+    if (A->on_device) {
+        hrp.resize(n + 1);
+        hci.resize(nnz);
+        if (cudaMemcpy(hrp.data(), A->row_ptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hci.data(), A->col, nnz * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CBG_ERR_CUDA;
+        rp = hrp.data();
+        ci = hci.data();
+    }
+    if (validate_csr_host(n, nnz, rp, ci)) return CBG_ERR_ARG;
+
+    cbg_handle* h = new (std::nothrow) cbg_handle();
+    if (!h) return CBG_ERR_OOM;
+    h->n = n;
+    h->nnz = nnz;
+    h->m = restart;
+    h->fmt = fmt;
+    h->opt = o;
+    h->stream = (cudaStream_t)o.stream;
+    h->ld = round_up(n, TILE_ROWS);
+    h->ldb = h->ld * fmt_bytes(fmt);
+    int rc = CBG_OK;
+#define TRY(x)                     \
+    do {                           \
+        rc = (x);                  \
+        if (rc) {                  \
+            free_handle(h);        \
+            return rc;             \
+        }                          \
+    } while (0)
+    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    TRY(dalloc(&h->rowptr, n + 1));
+    TRY(dalloc(&h->col, nnz));
+    TRY(dalloc(&h->val, nnz));
+    if (cudaMemcpy(h->rowptr, A->row_ptr, (n + 1) * sizeof(int), kind) != cudaSuccess ||
+        cudaMemcpy(h->col, A->col, nnz * sizeof(int), kind) != cudaSuccess ||
+        cudaMemcpy(h->val, A->val, nnz * sizeof(double), kind) != cudaSuccess)
+        TRY(CBG_ERR_CUDA);
+    TRY(dalloc(&h->scratch, 64));
+    if (o.precond == CBG_PC_JACOBI) {
+        TRY(dalloc(&h->dinv, h->ld));
+        TRY(dalloc(&h->valp, nnz));
+        int* bad = (int*)h->scratch;
+        cudaMemset(bad, 0, sizeof(int));
+        k_jacobi_prepare<<<1024, 256>>>(h->rowptr, h->col, h->val, n, h->dinv, bad);
+        k_scale_columns<<<2048, 256>>>(h->col, h->val, h->dinv, nnz, h->valp);
+        int hbad = 0;
+        if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        if (hbad) TRY(CBG_ERR_ARG);
+    }
+    TRY(dalloc(&h->V, (size_t)(restart + 1) * h->ldb));
+    if (cudaMemset(h->V, 0, (size_t)(restart + 1) * h->ldb) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    double** vecs[] = {&h->w, &h->w1, &h->w2, &h->r, &h->tmp, &h->z};
+    for (double** p : vecs) {
+        TRY(dalloc(p, h->ld));
+        if (cudaMemset(*p, 0, h->ld * sizeof(double)) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    }
+
+    // launch geometry
+    const Ops& op = ops_for(fmt);
+    const int sms = num_sms();
+    const int occ_dot = std::max(1, op.occ_dot());
+    const int occ_axpy = std::max(1, op.occ_axpy());
+    const int occ_spmv = std::max(1, spmv_occupancy());
+    const long long dot_tiles = h->ld / DOT_TR;
+    h->grid_dot = (int)std::min<long long>(dot_tiles, (long long)sms * occ_dot);
+    const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
+    h->grid_axpy = (int)std::min<long long>(axpy_blocks, (long long)sms * occ_axpy);
+    h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
+    h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
+    h->grid_spmv = (int)std::min<long long>((n * h->group + THREADS - 1) / THREADS, (long long)sms * occ_spmv);
+    h->grid_dot = std::max(1, h->grid_dot);
+    h->grid_axpy = std::max(1, h->grid_axpy);
+    h->grid_store = std::max(1, h->grid_store);
+    h->grid_spmv = std::max(1, h->grid_spmv);
+    h->gridmax = std::max(std::max(h->grid_dot, h->grid_axpy), std::max(h->grid_store, h->grid_spmv));
+
+    // state block: DevState + H, R, cs, sn, g, y, h, u, scales + partials + counters
+    const int m = restart, ldh = m + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off += (bytes + 255) / 256 * 256;
+        return o2;
+    };
+    size_t o_st = take(sizeof(DevState));
+    size_t o_H = take(sizeof(double) * ldh * m), o_R = take(sizeof(double) * ldh * m);
+    size_t o_cs = take(sizeof(double) * m), o_sn = take(sizeof(double) * m);
+    size_t o_g = take(sizeof(double) * ldh), o_y = take(sizeof(double) * ldh);
+    size_t o_h = take(sizeof(double) * ldh), o_u = take(sizeof(double) * ldh);
+    size_t o_sc = take(sizeof(double) * ldh);
+    size_t o_part = take(sizeof(double) * (size_t)h->gridmax * MAXCOLS);
+    size_t o_pn = take(sizeof(double) * (size_t)h->gridmax * 2);
+    size_t o_ps = take(sizeof(double) * (size_t)h->gridmax * 2);
+    size_t o_cnt = take(sizeof(unsigned int) * 16);
+    unsigned char* blk = nullptr;
+    TRY(dalloc(&blk, off));
+    h->state_block = blk;
+    if (cudaMemset(blk, 0, off) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    h->d.st = (DevState*)(blk + o_st);
+    h->d.H = (double*)(blk + o_H);
+    h->d.R = (double*)(blk + o_R);
+    h->d.cs = (double*)(blk + o_cs);
+    h->d.sn = (double*)(blk + o_sn);
+    h->d.g = (double*)(blk + o_g);
+    h->d.y = (double*)(blk + o_y);
+    h->d.h = (double*)(blk + o_h);
+    h->d.u = (double*)(blk + o_u);
+    h->d.scales = (double*)(blk + o_sc);
+    h->d.part = (double*)(blk + o_part);
+    h->d.part_norm = (double*)(blk + o_pn);
+    h->d.part_spmv = (double*)(blk + o_ps);
+    h->d.counters = (unsigned int*)(blk + o_cnt);
+    h->d.hist = nullptr;
+    if (cudaHostAlloc((void**)&h->flag_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    *h->flag_host = 0;
+    if (cudaHostGetDevicePointer((void**)&h->flag_dev, h->flag_host, 0) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    h->d.flag_host = h->flag_dev;
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    const int L = std::max(1, o.check_every);
+    h->step_ev.resize(L, nullptr);
+    for (auto& e : h->step_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    if (cudaDeviceSynchronize() != cudaSuccess) TRY(CBG_ERR_CUDA);
+#undef TRY
+    *out = h;
+    return CBG_OK;
+}
+
+int cbgmres_set_spai(cbg_handle* h, const double* pvals, int on_device)
+{
+    if (!h || !pvals) return CBG_ERR_ARG;
+    if (!h->pvals) {
+        int rc = dalloc(&h->pvals, h->nnz);
+        if (rc) return rc;
+    }
+    CBG_CUDA(cudaMemcpyAsync(h->pvals, pvals, h->nnz * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+int cbgmres_solve(cbg_handle* h, const double* b, double* x, double tol, int64_t maxit, cbg_stats* stats)
+{
+    if (!h) return CBG_ERR_ARG;
+    if (h->opt.precond == CBG_PC_SPAI && !h->pvals) return CBG_ERR_ARG;
+    return run_solve(h, b, x, tol, maxit, stats, 0);
+}
+
+int cbgmres_solve_host(cbg_handle* h, const double* b_host, double* x_host, double tol, int64_t maxit,
+                       cbg_stats* stats)
+{
+    if (!h || !b_host || !x_host) return CBG_ERR_ARG;
+    if (!h->bdev || !h->xdev) {
+        int rc = h->bdev ? CBG_OK : dalloc(&h->bdev, h->ld);
+        if (!rc && !h->xdev) rc = dalloc(&h->xdev, h->ld);
+        if (rc) return rc;
+    }
+    CBG_CUDA(cudaMemcpyAsync(h->bdev, b_host, h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CBG_CUDA(cudaMemcpyAsync(h->xdev, x_host, h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    int st = cbgmres_solve(h, h->bdev, h->xdev, tol, maxit, stats);
+    if (st < 0) return st;
+    CBG_CUDA(cudaMemcpyAsync(x_host, h->xdev, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+int cbgmres_arnoldi(cbg_handle* h, const double* b, const double* x0, int k, double* H_host, int* k_done)
+{
+    if (!h || !b || !x0 || k < 1 || k > h->m || !H_host || !k_done) return CBG_ERR_ARG;
+    if (!h->xdev) {
+        int rc0 = dalloc(&h->xdev, h->ld);
+        if (rc0) return rc0;
+        rc0 = dalloc(&h->bdev, h->ld);
+        if (rc0) return rc0;
+    }
+    double* x = h->xdev;   // work copy: the caller's x0 stays untouched
+    CBG_CUDA(cudaMemcpyAsync(x, x0, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    int st = run_solve(h, b, x, 0.0, k, nullptr, k);
+    if (st < 0) return st;
+    DevState hs{};
+    int rc = read_state(h, &hs);
+    if (rc) return rc;
+    // after the solve the residual kernel ran again; H of the first cycle is intact
+    const int kd = std::min(k, std::max(0, (int)std::min<long long>(hs.iters, k)));
+    std::vector<double> H((size_t)(h->m + 1) * h->m);
+    CBG_CUDA(cudaMemcpy(H.data(), h->d.H, H.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < kd; c++)
+        for (int i = 0; i <= kd; i++) H_host[i + (size_t)c * (kd + 1)] = H[i + (size_t)c * (h->m + 1)];
+    *k_done = kd;
+    return CBG_OK;
+}
+
+int cbgmres_basis_column(cbg_handle* h, int col, double* out)
+{
+    if (!h || col < 0 || col > h->m || !out) return CBG_ERR_ARG;
+    double sc = 1.0;
+    CBG_CUDA(cudaMemcpyAsync(&sc, h->d.scales + col, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    ops_for(h->fmt).decode(std::max(1, (int)std::min<long long>((h->n + THREADS - 1) / THREADS, 4096)), h->stream,
+                           h->V + (long long)col * h->ldb, h->n, sc, out);
+    CBG_CUDA(cudaGetLastError());
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+int cbgmres_spmv(cbg_handle* h, const double* x, double* y)
+{
+    if (!h || !x || !y) return CBG_ERR_ARG;
+    SpmvArgs a = spmv_args(h);
+    a.val = h->val;
+    a.x = x;
+    a.xscale = 1.0;
+    a.y = y;
+    spmv_f64(SPMV_PLAIN, h->group, h->grid_spmv, h->stream, a);
+    CBG_CUDA(cudaGetLastError());
+    CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+void cbgmres_destroy(cbg_handle* h)
+{
+    if (h) cudaStreamSynchronize(h->stream);
+    free_handle(h);
+}
+
+// ---------------------------------------------------------------- codec test kernels
+int cbg_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, double* scale_out, void* stream)
+{
+    if (fmt_bytes(fmt) == 0 || n < 0 || (n > 0 && (!v || !codes)) || !scale_out) return CBG_ERR_ARG;
+    EncParams ep = enc_params(fmt, vmax);
+    *scale_out = ep.scale;
+    if (n == 0) return CBG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int grid = (int)std::min<long long>((n + THREADS - 1) / THREADS, 8192);
+    ops_for(fmt).encode(grid, s, v, n, (unsigned char*)codes, ep);
+    CBG_CUDA(cudaGetLastError());
+    CBG_CUDA(cudaStreamSynchronize(s));
+    return CBG_OK;
+}
+
+int cbg_decode(int fmt, int64_t n, const void* codes, double scale, double* out, void* stream)
+{
+    if (fmt_bytes(fmt) == 0 || n < 0 || (n > 0 && (!codes || !out))) return CBG_ERR_ARG;
+    if (n == 0) return CBG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int grid = (int)std::min<long long>((n + THREADS - 1) / THREADS, 8192);
+    ops_for(fmt).decode(grid, s, (const unsigned char*)codes, n, scale, out);
+    CBG_CUDA(cudaGetLastError());
+    CBG_CUDA(cudaStreamSynchronize(s));
+    return CBG_OK;
+}
+
+// Standalone basis products (test access).  V must have ld % TILE_ROWS == 0 rows per
+// column and zero padding; w / the output vector must have ld elements.
+int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
+                  const double* w, double* hout, void* stream)
+{
+    if (fmt_bytes(fmt) == 0 || (arith != 0 && arith != 1) || n < 1 || ncols < 1 || ncols > MAXCOLS || !V ||
+        ld < n || ld % TILE_ROWS || !scales || !w || !hout)
+        return CBG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Ops& op = ops_for(fmt);
+    int grid = (int)std::min<long long>(ld / DOT_TR, (long long)num_sms() * std::max(1, op.occ_dot()));
+    double *part = nullptr, *sc = nullptr, *out = nullptr;
+    unsigned int* cnt = nullptr;
+    int rc = dalloc(&part, (size_t)grid * MAXCOLS);
+    if (!rc) rc = dalloc(&sc, ncols);
+    if (!rc) rc = dalloc(&out, ncols);
+    if (!rc) rc = dalloc(&cnt, 1);
+    if (!rc) {
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned int), s);
+        cudaMemcpyAsync(sc, scales, ncols * sizeof(double), cudaMemcpyHostToDevice, s);
+        DotArgs a{};
+        a.V = (const unsigned char*)V;
+        a.ldb = ld * fmt_bytes(fmt);
+        a.ncols = ncols;
+        a.scales = sc;
+        a.w = w;
+        a.nrows = ld;
+        a.part = part;
+        a.counter = cnt;
+        a.out = out;
+        op.dot(arith, grid, s, a);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hout, out, ncols * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = CBG_ERR_CUDA;
+    }
+    cudaFree(part); cudaFree(sc); cudaFree(out); cudaFree(cnt);
+    return rc;
+}
+
+int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
+                   const double* hcoef, double* w, void* stream)
+{
+    if (fmt_bytes(fmt) == 0 || (arith != 0 && arith != 1) || n < 1 || ncols < 1 || ncols > MAXCOLS || !V ||
+        ld < n || ld % TILE_ROWS || !scales || !hcoef || !w)
+        return CBG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Ops& op = ops_for(fmt);
+    const long long blocks = ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
+    int grid = (int)std::min<long long>(blocks, (long long)num_sms() * std::max(1, op.occ_axpy()));
+    double *sc = nullptr, *cf = nullptr, *pn = nullptr;
+    int rc = dalloc(&sc, ncols);
+    if (!rc) rc = dalloc(&cf, ncols);
+    if (!rc) rc = dalloc(&pn, (size_t)grid * 2);
+    if (!rc) {
+        cudaMemcpyAsync(sc, scales, ncols * sizeof(double), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(cf, hcoef, ncols * sizeof(double), cudaMemcpyHostToDevice, s);
+        AxpyArgs a{};
+        a.V = (const unsigned char*)V;
+        a.ldb = ld * fmt_bytes(fmt);
+        a.ncols = ncols;
+        a.scales = sc;
+        a.coef = cf;
+        a.sign = -1.0;
+        a.w_in = w;
+        a.w_out = w;
+        a.nrows = ld;
+        a.n = n;
+        a.part_norm = pn;
+        op.axpy(arith, EPI_SUB, grid, s, a);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = CBG_ERR_CUDA;
+    }
+    cudaFree(sc); cudaFree(cf); cudaFree(pn);
+    return rc;
+}
+
+int cbgmres_create_batched(int, const cbg_csr*, int, int, const cbg_options*, cbg_batch** out)
+{
+    if (out) *out = nullptr;
+    return CBG_ERR_UNSUPPORTED;
+}
+
+int cbgmres_solve_batched(cbg_batch*, const double* const*, double* const*, double, int64_t, cbg_stats*)
+{
+    return CBG_ERR_UNSUPPORTED;
+}
+
+void cbgmres_destroy_batched(cbg_batch*) {}
+
+}  // extern "C"

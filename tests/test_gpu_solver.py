@@ -1,0 +1,205 @@
+"""GPU solver parity against the CPU oracle (Fig. 1; Sections 4-5), through the C ABI.
+
+Bars: first 10 Hessenberg columns within 1e-10 (column-norm relative), iteration
+count within 2% (at least +-1 step), x within 1e-6 relative of the oracle's x, and the
+GPU's x meeting the 1e-10 true residual when the oracle recomputes it."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import FORMATS, col_relerr, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(name):
+    if name == "poisson64":
+        A = W.poisson2d(64); xs = W.exact_solution(A.n, 1)
+    elif name == "convdiff20":
+        A = W.convdiff3d(20); xs = W.exact_solution(A.n, 2)
+    elif name == "random27_small":
+        A = W.random27(20000, 0.1); xs = W.exact_solution(A.n, 3)
+    else:
+        raise ValueError(name)
+    return A, xs, W.rhs_from_solution(A, xs)
+
+
+@pytest.mark.parametrize("arith", ["df32", "fp64"])
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("prob", ["poisson64", "convdiff20", "random27_small"])
+def test_hessenberg_first_columns(prob, fmt, arith):
+    torch, cb = need_gpu()
+    A, xs, b = _problem(prob)
+    k = 10
+    ro = O.gmres(A, b, m=20, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True)
+    with cb.Solver.from_csr(A, restart=20, fmt=fmt, arith=arith) as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+    assert Hg.shape == (k + 1, k)
+    err = col_relerr(Hg, ro["H1"], k)
+    assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("prob", ["poisson64", "convdiff20"])
+def test_full_solve_parity(prob, fmt):
+    torch, cb = need_gpu()
+    A, xs, b = _problem(prob)
+    m, tol = 100, 1e-10
+    maxit = 20000
+    ro = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=tol, maxit=maxit)
+    assert ro["status"] == O.OK
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=m, fmt=fmt) as s:
+        st = s.solve(to_dev(torch, b), xg, tol=tol, maxit=maxit)
+    assert st["status"] == 0, st
+    x = xg.cpu().numpy()
+    # the oracle judges the GPU's answer
+    r = b - O.spmv(A, x)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+@pytest.mark.parametrize("arith", ["df32", "fp64"])
+def test_full_solve_fp64_modes_agree(arith):
+    torch, cb = need_gpu()
+    A, xs, b = _problem("random27_small")
+    ro = O.gmres(A, b, m=50, tol=1e-10, maxit=5000)
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=50, fmt="f32", arith=arith) as s:
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000)
+    assert st["status"] == 0
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(b - O.spmv(A, x)) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_jacobi_parity():
+    torch, cb = need_gpu()
+    A = W.diffusion3d_cc(16)[0]
+    xs = W.exact_solution(A.n, 5); b = W.rhs_from_solution(A, xs)
+    ro = O.gmres(A, b, m=40, fmt=O.F32, precond=O.PC_JACOBI, tol=1e-10, maxit=5000, want_H1=True)
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=40, fmt="f32", precond="jacobi") as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), 10)
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000)
+    assert np.all(col_relerr(Hg, ro["H1"], 10) <= 1e-10)
+    assert st["status"] == 0
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_spai_equal_to_jacobi_when_p_is_diagonal():
+    """P = D^{-1} on A's pattern (zeros off the diagonal) is the Jacobi preconditioner."""
+    torch, cb = need_gpu()
+    A = W.diffusion3d_cc(12)[0]
+    xs = W.exact_solution(A.n, 5); b = W.rhs_from_solution(A, xs)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    p = np.where(A.col == rows, 1.0 / A.val, 0.0)
+    ro = O.gmres(A, b, m=30, fmt=O.F32, precond=O.PC_SPAI, pvals=p, tol=1e-10, maxit=3000)
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=30, fmt="f32", precond="spai") as s:
+        s.set_spai(p)
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=3000)
+    assert st["status"] == 0
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
+    assert np.linalg.norm(xg.cpu().numpy() - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_spmv_parity():
+    torch, cb = need_gpu()
+    for A in (W.convdiff3d(16), W.random27(30000, 0.5)):
+        x = W.random_vector(A.n, 9)
+        with cb.Solver.from_csr(A, restart=4, fmt="f64") as s:
+            y = s.spmv(to_dev(torch, x)).cpu().numpy()
+        ref = O.spmv(A, x)
+        scale = np.abs(A.to_scipy()) @ np.abs(x)
+        assert np.all(np.abs(y - ref) <= 1e-15 * 30 * scale)
+
+
+def test_history_and_restart_behaviour():
+    torch, cb = need_gpu()
+    A, xs, b = _problem("poisson64")
+    ro = O.gmres(A, b, m=30, fmt=O.F32, tol=1e-10, maxit=5000, hist_cap=5000)
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=30, fmt="f32") as s:
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000, history=5000)
+    h = st["history"]
+    assert len(h) == st["iters"] and st["restarts"] >= 3
+    n = min(len(h), len(ro["hist"]), 30)
+    assert np.allclose(h[:n], ro["hist"][:n], rtol=1e-8, atol=1e-14)
+    for c0 in range(0, len(h), 30):
+        seg = h[c0:c0 + 30]
+        assert np.all(np.diff(seg) <= 1e-14 * seg[0])
+
+
+# ------------------------------------------------------------------------- edge cases
+def test_edge_cases():
+    torch, cb = need_gpu()
+    dev = lambda a: to_dev(torch, a)
+    # n = 1
+    A1 = W.from_dense(np.array([[4.0]]))
+    x = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A1, restart=3, fmt="f16") as s:
+        st = s.solve(dev([2.0]), x)
+    assert st["status"] == 0 and st["iters"] == 1 and x.item() == 0.5
+    # identity: one step; b = 0 gives x = 0; exact x0 needs no step
+    A = W.from_dense(np.eye(50))
+    b = np.arange(1.0, 51.0)
+    with cb.Solver.from_csr(A, restart=5, fmt="f64") as s:
+        x = torch.zeros(50, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(b), x, tol=1e-14)
+        assert st["status"] == 0 and st["iters"] == 1
+        assert np.allclose(x.cpu().numpy(), b, rtol=1e-13, atol=0)
+        x = torch.ones(50, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(np.zeros(50)), x)
+        assert st["status"] == 0 and st["iters"] == 0 and float(x.abs().max()) == 0.0
+        x = dev(b)
+        st = s.solve(dev(b), x)
+        assert st["status"] == 0 and st["iters"] == 0
+    # maxit
+    A, xs, bb = _problem("poisson64")
+    with cb.Solver.from_csr(A, restart=10, fmt="f64") as s:
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(bb), x, tol=1e-12, maxit=7)
+        assert st["status"] == 1 and st["iters"] == 7
+        ro = O.gmres(A, bb, m=10, tol=1e-12, maxit=7)
+        assert np.linalg.norm(x.cpu().numpy() - ro["x"]) <= 1e-10 * np.linalg.norm(ro["x"])
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(dev(bb), x, tol=1e-12, maxit=0)
+        assert st["status"] == 1 and st["iters"] == 0
+        # non-finite input
+        bad = bb.copy(); bad[17] = np.nan
+        with pytest.raises(cb.CbgError) as e:
+            s.solve(dev(bad), torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+        assert e.value.status == -2
+
+
+def test_create_rejects_bad_input():
+    torch, cb = need_gpu()
+    A = W.poisson2d(8)
+    bad_col = A.col.copy(); bad_col[5] = A.n
+    with pytest.raises(cb.CbgError):
+        cb.Solver(A.rowptr, bad_col, A.val, restart=5)
+    with pytest.raises(cb.CbgError):
+        cb.Solver(A.rowptr, A.col, A.val, restart=0)
+    with pytest.raises(cb.CbgError):
+        cb.Solver(A.rowptr, A.col, A.val, restart=300)
+    a = np.array([[0.0, 1.0], [1.0, 0.0]])
+    Z = W.from_dense(a)
+    with pytest.raises(cb.CbgError):
+        cb.Solver.from_csr(Z, restart=2, precond="jacobi")
+
+
+def test_solve_host_matches_device():
+    torch, cb = need_gpu()
+    A, xs, b = _problem("convdiff20")
+    with cb.Solver.from_csr(A, restart=50, fmt="f32") as s:
+        xh = np.zeros(A.n)
+        st_h = s.solve_host(b, xh, tol=1e-10, maxit=5000)
+        xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st_d = s.solve(to_dev(torch, b), xd, tol=1e-10, maxit=5000)
+    assert st_h["status"] == 0 and st_h["iters"] == st_d["iters"]
+    assert np.array_equal(xh, xd.cpu().numpy())
