@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of compressed-basis GMRES on GB300.
+
+Workload: 3D convection-diffusion on a 128^3 grid (n = 2,097,152, 14,581,760 nnz,
+7-point upwind stencil, Pe = 10), b = A x* with seeded x* ~ U[-1,1], x0 = 0,
+restart m = 100, CGS with one re-orthogonalisation pass, tol 1e-10 relative true
+residual.  One step = one time-to-solution for every basis format of the workload
+(f64, f32, f16, i32, i16), inputs resident in HBM.
+
+Metric: time-to-1e-10 residual speedup of CB-GMRES (f32 basis, the paper's
+recommended format) over FP64-basis GMRES run by the same library on the same GPU;
+alongside it the achieved HBM bandwidth of the basis-GEMV kernels (roofline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank solves its own
+replica of the system (the single-system solve has no data-parallel split without a
+halo exchange); times are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 residual speedup vs FP64-basis GMRES; basis-GEMV HBM GB/s"
+WORKLOAD = "convdiff3d_128^3_pe10_upwind_restart100_tol1e-10"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--formats", default="f64,f32,f16,i32,i16")
+    p.add_argument("--headline", default="f32")
+    p.add_argument("--arith", default="df32")
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--maxit", type=int, default=40000)
+    p.add_argument("--restart", type=int, default=100)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region (read only)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic_per_element(fmt: str):
+    """DRAM bytes per basis element of the basis-GEMV kernels from the committed ncu
+    summary (profiles/basis_gemv_ncu.md, line `traffic_bytes_per_element <cls> <fmt> <x>`)."""
+    path = os.path.join(ROOT, "profiles", "basis_gemv_ncu.md")
+    out = {}
+    try:
+        with open(path) as f:
+            for ln in f:
+                t = ln.strip().strip("`").split()
+                if len(t) == 4 and t[0] == "traffic_bytes_per_element" and t[2] == fmt:
+                    out[t[1]] = float(t[3])
+    except OSError:
+        pass
+    return out
+
+
+def build_problem(grid: int):
+    import workloads as W
+    A = W.convdiff3d(grid)
+    xs = W.exact_solution(A.n, 2)
+    b = W.rhs_from_solution(A, xs)
+    return A, xs, b
+
+
+def oracle_sample(A, b, fmt: str, steps: int, restart: int):
+    """Time the oracle (as it stands) on the first `steps` Arnoldi steps of the solve."""
+    import oracle as O
+    t0 = time.perf_counter()
+    r = O.gmres(A, b, m=restart, fmt=O.FORMATS[fmt], tol=0.0, maxit=steps)
+    return time.perf_counter() - t0, r["iters"]
+
+
+# ------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, xs, b = build_problem(args.grid)
+    steps = max(2, min(args.cpu_steps, 12))
+    times = {"f64": [], args.headline: []}
+    for it in range(args.warmup + args.steps):
+        for fmt in times:
+            t, _ = oracle_sample(A, b, fmt, steps, args.restart)
+            if it >= args.warmup:
+                times[fmt].append(t)
+    t64 = sum(times["f64"]); th = sum(times[args.headline])
+    v = t64 / th
+    sample = (f"first {steps} Arnoldi steps of the {WORKLOAD} solve with the f64 and {args.headline} "
+              f"basis, oracle (plain C, sequential), per step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "x", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1000 * (t64 + th) / args.steps,
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "restart": args.restart,
+                       "headline_format": args.headline, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "x", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "x", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2009_12101_gb300 as cb
+    cb.ensure_built()
+    cb.lib()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    fmts = args.formats.split(",")
+    if "f64" not in fmts:
+        fmts = ["f64"] + fmts
+    A, xs, b = build_problem(args.grid)
+    n = A.n
+    stream = torch.cuda.current_stream()
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, profile=True)
+               for f in fmts}
+
+    def solve_all(record):
+        out = {}
+        for f in fmts:
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solvers[f].solve(bd, x, tol=args.tol, maxit=args.maxit)
+            e1.record(stream)
+            out[f] = (e0, e1, st)
+        return out
+
+    for _ in range(args.warmup):
+        solve_all(False)
+    for s in solvers.values():
+        s.profile(reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    runs = [solve_all(True) for _ in range(args.steps)]
+    g1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = g0.elapsed_time(g1)
+
+    per_fmt = {f: [r[f][0].elapsed_time(r[f][1]) for r in runs] for f in fmts}
+    stats = {f: runs[-1][f][2] for f in fmts}
+    launches = sum(r[f][2]["kernel_launches"] for r in runs for f in fmts)
+    t_fmt = {f: sum(v) / len(v) for f, v in per_fmt.items()}
+    if world > 1:
+        t = torch.tensor([t_fmt[f] for f in fmts], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_fmt = {f: float(t[i]) for i, f in enumerate(fmts)}
+    speedup = {f: t_fmt["f64"] / t_fmt[f] for f in fmts}
+    value = speedup[args.headline]
+
+    # live roofline of the basis GEMV kernels (headline format, timed region)
+    peak, peak_kind = measured_peaks()
+    prof = {f: solvers[f].profile() for f in fmts}
+    ph = prof[args.headline]
+    cls = max(("basis_dot", "basis_axpy"), key=lambda c: ph[c]["ms"])
+    launches_cls = max(1, ph[cls]["launches"])
+    avg_ms = ph[cls]["ms"] / launches_cls
+    avg_bytes = ph[cls]["bytes"] / launches_cls
+    achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+    tpe = ncu_traffic_per_element(args.headline).get(cls)
+    fb = cb.FORMAT_BYTES[args.headline]
+    traffic = tpe * (avg_bytes / fb) if tpe else None
+    gemv = {}
+    for f in fmts:
+        for c in ("basis_dot", "basis_axpy"):
+            p = prof[f][c]
+            if p["ms"] > 0:
+                gemv[f"{f}/{c}"] = round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)
+    roofline = {"bound": "hbm", "kernel": f"k_basis_{cls.split('_')[1]} ({args.headline}, {args.arith})",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+                "basis_gemv_gbs_by_format": gemv}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        bh = torch.from_numpy(b).pin_memory().numpy()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+        te = {}
+        for f in ("f64", args.headline):
+            ts = []
+            for _ in range(max(1, args.steps)):
+                xh[:] = 0.0
+                barrier()
+                t0 = time.perf_counter()
+                solvers[f].solve_host(bh, xh, tol=args.tol, maxit=args.maxit)
+                ts.append(time.perf_counter() - t0)
+            te[f] = sum(ts) / len(ts)
+        if world > 1:
+            t = torch.tensor([te["f64"], te[args.headline]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = {"f64": float(t[0]), args.headline: float(t[1])}
+        e2e = {"value": te["f64"] / te[args.headline], "unit": "x",
+               "h2d_bytes_per_step": 2 * 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n,
+               "seconds": {k: round(v, 4) for k, v in te.items()}}
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t64, it = oracle_sample(A, b, "f64", args.cpu_steps, args.restart)
+        th, _ = oracle_sample(A, b, args.headline, args.cpu_steps, args.restart)
+        gpu_step_ms = {f: t_fmt[f] / max(1, stats[f]["iters"]) for f in ("f64", args.headline)}
+        cpu = {"value": t64 / th, "unit": "x", "cores": 1, "kind": "oracle",
+               "sample": (f"first {args.cpu_steps} Arnoldi steps (j = 1..{args.cpu_steps}) of the "
+                          f"{WORKLOAD} solve, f64 and {args.headline} basis, sequential C oracle"),
+               "oracle_ms_per_step": {"f64": 1000 * t64 / it, args.headline: 1000 * th / it},
+               "gpu_ms_per_step_full_solve": gpu_step_ms}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "x", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "df32" if args.arith == "df32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": A.nnz, "restart": args.restart,
+                       "tol": args.tol, "headline_format": args.headline, "formats": fmts,
+                       "arith": ("basis products in double-float (FP32 pairs), SpMV/norms/Givens/"
+                                 "least squares in FP64" if args.arith == "df32" else "all FP64"),
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+                       "l2": "no flush: every basis (>= 0.4 GB per format) exceeds the 129 MB L2"},
+            "time_to_solution_s": {f: round(t_fmt[f] / 1000, 4) for f in fmts},
+            "speedup_vs_f64": {f: round(v, 4) for f, v in speedup.items()},
+            "iterations": {f: stats[f]["iters"] for f in fmts},
+            "true_relres": {f: stats[f]["true_relres"] for f in fmts},
+            "status": {f: stats[f]["status"] for f in fmts},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for s in solvers.values():
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

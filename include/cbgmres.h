@@ -89,7 +89,10 @@ typedef struct {
     double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
     void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
     int32_t check_every;     /* host polls the convergence flag every k steps (4)      */
-    int32_t use_graph;       /* 1: replay the Arnoldi steps from CUDA graphs (1)       */
+    int32_t use_graph;       /* reserved, must be 0                                     */
+    int32_t profile;         /* 1: time every kernel launch with CUDA events recorded on
+                                options.stream (read with cbgmres_profile)              */
+    int32_t pad0;
 } cbg_options;
 
 typedef struct {
@@ -105,7 +108,20 @@ typedef struct {
     double* history;         /* optional host buffer: recurrence residual per step     */
     int64_t history_cap;     /* its capacity (0: none)                                  */
     int64_t history_len;     /* entries written                                         */
+    int64_t kernel_launches; /* library kernels launched by this call                   */
 } cbg_stats;
+
+/* Per-kernel-class timing gathered while options.profile == 1 (accumulated over
+ * solves until cbgmres_profile(..., reset = 1)).  Classes: 0 basis dot (V^T w),
+ * 1 basis axpy (w - V h), 2 SpMV (Arnoldi and residual), 3 store/finalize, 4 other.
+ * ms: summed CUDA-event durations; bytes: algorithmic HBM bytes (basis codes read for
+ * classes 0-1: columns * n * bytes(fmt); CSR + vectors for class 2; codes written plus
+ * w read for class 3); launches: count. */
+typedef struct {
+    double ms[5];
+    double bytes[5];
+    int64_t launches[5];
+} cbg_profile;
 
 typedef struct cbg_handle cbg_handle;
 typedef struct cbg_batch cbg_batch;
@@ -177,6 +193,10 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
                   const double* scales, const double* w, double* h, void* stream);
 int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
                    const double* scales, const double* h, double* w, void* stream);
+
+/* Copy the accumulated per-kernel profile of a handle (options.profile == 1) into
+ * *out; reset != 0 clears it afterwards.  Errors: CBG_ERR_ARG. */
+int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset);
 
 /* y = A x with the library's SpMV (device x, y).  For parity checks. */
 int cbgmres_spmv(cbg_handle* h, const double* x, double* y);

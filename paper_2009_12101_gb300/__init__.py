@@ -44,14 +44,23 @@ class Csr(C.Structure):
 class Options(C.Structure):
     _fields_ = [("reorth", C.c_int32), ("precond", C.c_int32), ("arith", C.c_int32),
                 ("spmv_group", C.c_int32), ("eta", C.c_double), ("breakdown_eps", C.c_double),
-                ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32)]
+                ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32),
+                ("profile", C.c_int32), ("pad0", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("reorths", C.c_int64),
                 ("true_relres", C.c_double), ("est_relres", C.c_double), ("ms_total", C.c_double),
                 ("bytes_model", C.c_double), ("status", C.c_int32), ("pad0", C.c_int32),
-                ("history", C.c_void_p), ("history_cap", C.c_int64), ("history_len", C.c_int64)]
+                ("history", C.c_void_p), ("history_cap", C.c_int64), ("history_len", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 5), ("bytes", C.c_double * 5), ("launches", C.c_int64 * 5)]
+
+
+PROFILE_CLASSES = ("basis_dot", "basis_axpy", "spmv", "store", "other")
 
 
 _lib = None
@@ -85,6 +94,7 @@ def lib():
             L.cbgmres_arnoldi.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_int)]
             L.cbgmres_basis_column.argtypes = [vp, i32, vp]
             L.cbgmres_spmv.argtypes = [vp, vp, vp]
+            L.cbgmres_profile.argtypes = [vp, C.POINTER(Profile), i32]
             L.cbgmres_destroy.argtypes = [vp]
             L.cbgmres_destroy.restype = None
             L.cbg_encode.argtypes = [i32, i64, vp, d, vp, C.POINTER(d), vp]
@@ -128,7 +138,7 @@ def _dev_f64(t, n=None, name="vector"):
 
 
 def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=None,
-            check_every=4, eta=None, breakdown_eps=None) -> Options:
+            check_every=4, eta=None, breakdown_eps=None, profile=False) -> Options:
     o = Options()
     lib().cbgmres_options_default(C.byref(o))
     o.precond = PRECONDS[precond]
@@ -136,6 +146,7 @@ def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=
     o.reorth = REORTH[reorth]
     o.spmv_group = spmv_group
     o.check_every = check_every
+    o.profile = int(bool(profile))
     if eta is not None:
         o.eta = eta
     if breakdown_eps is not None:
@@ -146,7 +157,7 @@ def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=
 
 def _stats_dict(st: Stats, hist=None) -> dict:
     out = {k: getattr(st, k) for k in ("iters", "restarts", "reorths", "true_relres", "est_relres",
-                                       "ms_total", "bytes_model", "status")}
+                                       "ms_total", "bytes_model", "status", "kernel_launches")}
     if hist is not None:
         out["history"] = hist[: st.history_len].copy()
     return out
@@ -160,7 +171,7 @@ class Solver:
 
     def __init__(self, rowptr, col, val, *, restart: int = 100, fmt: str = "f64",
                  precond: str = "none", arith: str = "df32", reorth: str = "always",
-                 spmv_group: int = 0, stream=None, check_every: int = 4):
+                 spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False):
         torch = _torch()
         L = lib()
         self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
@@ -177,7 +188,7 @@ class Solver:
         self.n, self.nnz = int(csr.n), int(csr.nnz)
         self.ld = (self.n + TILE_ROWS - 1) // TILE_ROWS * TILE_ROWS
         opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
-                      stream=stream, check_every=check_every)
+                      stream=stream, check_every=check_every, profile=profile)
         h = C.c_void_p()
         _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
                "cbgmres_create")
@@ -248,6 +259,13 @@ class Solver:
         _check(lib().cbgmres_basis_column(self._h, col, C.c_void_p(out.data_ptr())),
                "cbgmres_basis_column")
         return out
+
+    def profile(self, reset: bool = False) -> dict:
+        """Per-kernel-class CUDA-event timings (needs profile=True at construction)."""
+        p = Profile()
+        _check(lib().cbgmres_profile(self._h, C.byref(p), int(reset)), "cbgmres_profile")
+        return {c: {"ms": p.ms[i], "bytes": p.bytes[i], "launches": p.launches[i]}
+                for i, c in enumerate(PROFILE_CLASSES)}
 
     def spmv(self, x):
         torch = _torch()

@@ -225,6 +225,13 @@ struct cbg_handle {
     int grid_dot = 0, grid_axpy = 0, grid_store = 0, grid_spmv = 0, group = 1, gridmax = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> step_ev;
+    // launch accounting and optional per-kernel profiling
+    long long launches = 0;
+    std::vector<cudaEvent_t> prof_ev;      // pool of event pairs
+    std::vector<int> prof_cls;             // class of each recorded pair
+    std::vector<double> prof_bytes;        // algorithmic bytes of each pair
+    int prof_used = 0;
+    cbg_profile prof{};
 };
 
 namespace {
@@ -240,6 +247,7 @@ void free_handle(cbg_handle* h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto e : h->step_ev) cudaEventDestroy(e);
+    for (auto e : h->prof_ev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -275,6 +283,46 @@ int pick_group(long long n, long long nnz)
     return 32;
 }
 
+// ------------------------------------------------------------- profiling of launches
+// Every library launch goes through `launch`, which counts it and, with profiling on,
+// brackets it with a pair of events recorded on the handle's stream.
+void harvest_profile(cbg_handle* h)
+{
+    // all recorded pairs precede a completed stream synchronisation
+    for (int i = 0; i < h->prof_used; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) == cudaSuccess) {
+            const int c = h->prof_cls[i];
+            h->prof.ms[c] += ms;
+            h->prof.bytes[c] += h->prof_bytes[i];
+            h->prof.launches[c] += 1;
+        }
+    }
+    h->prof_used = 0;
+}
+
+template <class F> void launch(cbg_handle* h, int cls, double bytes, F&& f)
+{
+    h->launches++;
+    const bool prof = h->opt.profile && h->prof_used < (int)h->prof_cls.size();
+    if (prof) cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
+    f();
+    if (prof) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], h->stream);
+        h->prof_cls[h->prof_used] = cls;
+        h->prof_bytes[h->prof_used] = bytes;
+        h->prof_used++;
+    }
+}
+
+// algorithmic HBM bytes of one SpMV (CSR values + indices + row pointers, x read, y
+// written) and of one store (w read, codes written)
+double spmv_bytes(const cbg_handle* h)
+{
+    return (double)h->nnz * 12.0 + (double)(h->n + 1) * 4.0 + 16.0 * (double)h->n;
+}
+double store_bytes(const cbg_handle* h) { return (double)h->n * (8.0 + (double)fmt_bytes(h->fmt)); }
+
 // ------------------------------------------------------------------ launches per step
 SpmvArgs spmv_args(cbg_handle* h)
 {
@@ -296,7 +344,7 @@ void enqueue_residual(cbg_handle* h, const double* b, const double* x)
     a.b = b;
     a.y = h->r;
     a.counter = h->d.counters + 0;
-    spmv_f64(SPMV_RESIDUAL, h->group, h->grid_spmv, h->stream, a);
+    launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_RESIDUAL, h->group, h->grid_spmv, h->stream, a); });
 }
 
 void enqueue_step(cbg_handle* h, int j)
@@ -314,7 +362,7 @@ void enqueue_step(cbg_handle* h, int j)
         if (h->opt.precond == CBG_PC_SPAI) {
             a.val = h->pvals;
             a.y = h->z;
-            op.spmv_code(SPMV_PLAIN, h->group, h->grid_spmv, s, a);   // z = P v
+            launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_PLAIN, h->group, h->grid_spmv, s, a); });   // z = P v
             SpmvArgs b2 = spmv_args(h);
             b2.active = active;
             b2.val = h->val;
@@ -322,16 +370,17 @@ void enqueue_step(cbg_handle* h, int j)
             b2.xscale = 1.0;
             b2.y = h->w;
             b2.counter = h->d.counters + 1;
-            spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2);     // w = A z
+            launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
         } else {
             a.val = h->valp ? h->valp : h->val;
             a.y = h->w;
             a.counter = h->d.counters + 1;
-            op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a);
+            launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
         }
     }
     const int ncols = j + 1;
     const bool reorth = h->opt.reorth != CBG_REORTH_NEVER;
+    const double pass_bytes = (double)ncols * (double)h->n * (double)fmt_bytes(h->fmt);
     // step 5: h = V^T w ; w1 = w - V h
     DotArgs da{};
     da.V = h->V;
@@ -344,7 +393,7 @@ void enqueue_step(cbg_handle* h, int j)
     da.w = h->w;
     da.counter = h->d.counters + 2;
     da.out = h->d.h;
-    op.dot(h->opt.arith, h->grid_dot, s, da);
+    launch(h, 0, pass_bytes, [&] { op.dot(h->opt.arith, h->grid_dot, s, da); });
 
     AxpyArgs xa{};
     xa.V = h->V;
@@ -359,17 +408,17 @@ void enqueue_step(cbg_handle* h, int j)
     xa.coef = h->d.h;
     xa.w_in = h->w;
     xa.w_out = reorth ? h->w1 : h->w2;
-    op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa);
+    launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     if (reorth) {
         // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
         da.w = h->w1;
         da.counter = h->d.counters + 3;
         da.out = h->d.u;
-        op.dot(h->opt.arith, h->grid_dot, s, da);
+        launch(h, 0, pass_bytes, [&] { op.dot(h->opt.arith, h->grid_dot, s, da); });
         xa.coef = h->d.u;
         xa.w_in = h->w1;
         xa.w_out = h->w2;
-        op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa);
+        launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     }
     // steps 6, 12-14 and the Givens update
     StoreArgs sa{};
@@ -384,7 +433,7 @@ void enqueue_step(cbg_handle* h, int j)
     sa.nparts = h->grid_axpy;
     sa.n = h->n;
     sa.fmt = h->fmt;
-    op.store(h->grid_store, s, sa);
+    launch(h, 3, store_bytes(h), [&] { op.store(h->grid_store, s, sa); });
 }
 
 void enqueue_first_vector(cbg_handle* h)
@@ -400,13 +449,13 @@ void enqueue_first_vector(cbg_handle* h)
     sa.nparts = 0;
     sa.n = h->n;
     sa.fmt = h->fmt;
-    ops_for(h->fmt).store(h->grid_store, h->stream, sa);
+    launch(h, 3, store_bytes(h), [&] { ops_for(h->fmt).store(h->grid_store, h->stream, sa); });
 }
 
 void enqueue_cycle_end(cbg_handle* h, double* x)
 {
     cudaStream_t s = h->stream;
-    k_backsolve<<<1, 32, 0, s>>>(h->d);
+    launch(h, 4, 0.0, [&] { k_backsolve<<<1, 32, 0, s>>>(h->d); });
     const Ops& op = ops_for(h->fmt);
     AxpyArgs xa{};
     xa.V = h->V;
@@ -420,17 +469,17 @@ void enqueue_cycle_end(cbg_handle* h, double* x)
     xa.n = h->n;
     if (h->opt.precond == CBG_PC_SPAI) {
         xa.w_out = h->tmp;
-        op.axpy(h->opt.arith, EPI_PLAIN, h->grid_axpy, s, xa);       // t = V y
+        launch(h, 4, 0.0, [&] { op.axpy(h->opt.arith, EPI_PLAIN, h->grid_axpy, s, xa); });       // t = V y
         SpmvArgs a = spmv_args(h);
         a.val = h->pvals;
         a.x = h->tmp;
         a.xscale = 1.0;
         a.y = x;
-        spmv_f64(SPMV_ACCUM, h->group, h->grid_spmv, s, a);           // x += P t
+        launch(h, 4, 0.0, [&] { spmv_f64(SPMV_ACCUM, h->group, h->grid_spmv, s, a); });           // x += P t
     } else {
         xa.w_out = x;
         xa.dinv = h->opt.precond == CBG_PC_JACOBI ? h->dinv : nullptr;
-        op.axpy(h->opt.arith, EPI_XUPD, h->grid_axpy, s, xa);        // x += D^{-1} V y
+        launch(h, 4, 0.0, [&] { op.axpy(h->opt.arith, EPI_XUPD, h->grid_axpy, s, xa); });        // x += D^{-1} V y
     }
 }
 
@@ -454,8 +503,9 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
     cudaStream_t s = h->stream;
     CBG_CUDA(cudaEventRecord(h->ev0, s));
     // ||b|| and finiteness of b and x0
-    k_norm_check<<<1, THREADS, 0, s>>>(b, h->n, h->scratch);
-    k_norm_check<<<1, THREADS, 0, s>>>(x, h->n, h->scratch + 2);
+    const long long launches0 = h->launches;
+    launch(h, 4, 0.0, [&] { k_norm_check<<<1, THREADS, 0, s>>>(b, h->n, h->scratch); });
+    launch(h, 4, 0.0, [&] { k_norm_check<<<1, THREADS, 0, s>>>(x, h->n, h->scratch + 2); });
     double nb[4];
     CBG_CUDA(cudaMemcpyAsync(nb, h->scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CBG_CUDA(cudaStreamSynchronize(s));
@@ -480,16 +530,19 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
         }
         const double target = tol * bnorm;
         const long long maxit_eff = k_only > 0 ? std::min<long long>(maxit, k_only) : maxit;
-        k_init_state<<<1, 1, 0, s>>>(h->d.st, bnorm, target, h->opt.breakdown_eps, h->m, hist_cap > 0,
-                                     hist_cap);
+        launch(h, 4, 0.0, [&] {
+            k_init_state<<<1, 1, 0, s>>>(h->d.st, bnorm, target, h->opt.breakdown_eps, h->m, hist_cap > 0,
+                                         hist_cap);
+        });
         const double spmv_bytes = (double)h->nnz * 12.0 + (double)(h->n + 1) * 4.0 + 16.0 * (double)h->n;
         const int L = (int)h->step_ev.size();
         long long iters_before = -1;
         for (;;) {
             enqueue_residual(h, b, x);
-            k_cycle_start<<<1, 1, 0, s>>>(h->d, maxit_eff, h->m);
+            launch(h, 4, 0.0, [&] { k_cycle_start<<<1, 1, 0, s>>>(h->d, maxit_eff, h->m); });
             int rc = read_state(h, &hs);
             if (rc) return rc;
+            harvest_profile(h);
             for (int j = 0; j < hs.last_k; j++)
                 bytes += spmv_bytes + 4.0 * (double)(j + 1) * (double)h->n * (double)fmt_bytes(h->fmt);
             if (!hs.active) break;
@@ -518,7 +571,9 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
     CBG_CUDA(cudaEventRecord(h->ev1, s));
     CBG_CUDA(cudaEventSynchronize(h->ev1));
     CBG_CUDA(cudaGetLastError());
+    harvest_profile(h);
     if (stats) {
+        stats->kernel_launches = h->launches - launches0;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);
         stats->iters = hs.iters;
@@ -558,6 +613,7 @@ void cbgmres_options_default(cbg_options* o)
     o->stream = nullptr;
     o->check_every = 4;
     o->use_graph = 0;
+    o->profile = 0;
 }
 
 const char* cbgmres_status_string(int s)
@@ -722,6 +778,14 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->step_ev.resize(L, nullptr);
     for (auto& e : h->step_ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    if (o.profile) {
+        const int pairs = 8 * restart + 64;
+        h->prof_ev.resize(2 * pairs, nullptr);
+        h->prof_cls.resize(pairs, 0);
+        h->prof_bytes.resize(pairs, 0.0);
+        for (auto& e : h->prof_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) TRY(CBG_ERR_CUDA);
 #undef TRY
     *out = h;
@@ -802,6 +866,14 @@ int cbgmres_basis_column(cbg_handle* h, int col, double* out)
                            h->V + (long long)col * h->ldb, h->n, sc, out);
     CBG_CUDA(cudaGetLastError());
     CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset)
+{
+    if (!h || !out) return CBG_ERR_ARG;
+    *out = h->prof;
+    if (reset) h->prof = cbg_profile{};
     return CBG_OK;
 }
 
