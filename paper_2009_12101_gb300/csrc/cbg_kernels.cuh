@@ -14,8 +14,8 @@ namespace cbg {
 
 constexpr int THREADS = 256;
 constexpr int TILE_ROWS = 4096;      // ld (padded rows) is a multiple of this
-constexpr int DOT_TR = 1024;         // rows of w staged in shared memory per dot tile
 constexpr int MAXCOLS = 256;         // largest restart length + 1 supported by the kernels
+constexpr int DOT_MIN_ROWS = 1024;   // the dot kernel's grid gives every block >= this many rows
 constexpr int ARITH_DF32 = 0;
 constexpr int ARITH_FP64 = 1;
 
@@ -92,23 +92,30 @@ __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& 
     }
 }
 
-// padded shared-memory index of row r of a staged w tile (conflict-free 16-B reads by
-// four row subgroups of a warp)
-template <int E> __device__ __forceinline__ int ws_idx(int r) { return r + 2 * (r / E); }
+// Rows of w held in shared memory per chunk of the dot kernel, and the padded index
+// of row r: four row subgroups of a warp read E consecutive rows each (E * 8 bytes
+// apart); for E >= 8 their 16-byte reads would share banks, so 16 bytes of padding
+// follow every E rows (a lane's E rows stay contiguous).
+constexpr int DOT_ROWS = 4096;
+template <int E> __device__ __forceinline__ int ws_idx(int r) { return E >= 8 ? r + 2 * (r / E) : r; }
+template <int E> struct WsLen { static constexpr int value = E >= 8 ? DOT_ROWS + DOT_ROWS / 4 : DOT_ROWS; };
 
 // ============================================================== h = V^T w  (steps 5, 8)
-// Lane-per-column schedule: lane l of a warp owns column cg*8 + (l & 7) and row
-// subgroup l >> 3; its 16-byte loads walk down that column, w comes from shared memory
-// as a broadcast, and the partial sum for the column stays in the lane's registers
-// until the block ends.  No per-column reduction inside the hot loop.
+// Lane-per-column schedule: lane l of a warp owns column 8*cg + (l & 7) and row
+// subgroup l >> 3; its 16-byte loads walk down that column (eight in flight), w comes
+// from shared memory as a broadcast, and the column's partial sum stays in the lane's
+// registers until the block ends.  Each block owns one contiguous row range (persistent
+// grid of about two blocks per SM) and stages w for it in chunks of DOT_ROWS rows, so
+// there is one barrier per chunk and none in the streaming loop.  Blocks leave per-column
+// partials; the last block to finish adds them in a fixed order (deterministic).
 struct DotArgs {
     const unsigned char* V;
     long long ldb;            // bytes per column
     int ncols;
-    const int* ncols_dev;     // if non-null, read ncols from device (columns k..)
+    const int* ncols_dev;     // if non-null, read ncols from device
     const double* scales;
     const double* w;          // FP64 vector, ld elements
-    long long nrows;          // ld (multiple of DOT_TR)
+    long long nrows;          // ld (multiple of TILE_ROWS)
     double* part;             // [gridDim.x][MAXCOLS]
     unsigned int* counter;
     double* out;              // [ncols]
@@ -116,14 +123,14 @@ struct DotArgs {
 };
 
 template <int FMT, int ARITH>
-__global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
+__global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
 {
     if (a.active && *a.active == 0) return;
     constexpr int BS = FmtInfo<FMT>::bytes;
     constexpr int E = 16 / BS;
-    constexpr int STEPS = DOT_TR / (4 * E);
-    constexpr int MAXP = 4;                        // pairs per warp (MAXCOLS/8/8)
-    __shared__ __align__(16) float2 ws[DOT_TR + 2 * (DOT_TR / E)];
+    constexpr int MAXP = 4;                        // pairs per warp (MAXCOLS / 8 / 8)
+    constexpr int U = 8;                           // loads in flight per lane
+    __shared__ __align__(16) float2 ws[WsLen<E>::value];
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ncg = (ncols + 7) >> 3;
@@ -131,23 +138,28 @@ __global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
     const int npairs = ncg * nph;
     const int sub = lane >> 3;
 
+    // contiguous row range of this block (multiples of 64 rows)
+    const long long per = ((a.nrows + gridDim.x - 1) / gridDim.x + 63) / 64 * 64;
+    const long long rb = (long long)blockIdx.x * per;
+    const long long re = rb + per < a.nrows ? rb + per : a.nrows;
+
     float aS[MAXP], aC[MAXP];
     double aD[MAXP];
 #pragma unroll
     for (int p = 0; p < MAXP; p++) { aS[p] = 0.f; aC[p] = 0.f; aD[p] = 0.0; }
 
-    const long long ntiles = a.nrows / DOT_TR;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long r0 = t * DOT_TR;
+    for (long long c0 = rb; c0 < re; c0 += DOT_ROWS) {
+        const int rows = (int)(re - c0 < DOT_ROWS ? re - c0 : DOT_ROWS);
         __syncthreads();
-        for (int r = threadIdx.x; r < DOT_TR; r += THREADS) {
-            double wv = a.w[r0 + r];
-            float2 s;
-            if constexpr (ARITH == ARITH_DF32) split_f64(wv, s.x, s.y);
-            else s = *reinterpret_cast<float2*>(&wv);
-            ws[ws_idx<E>(r)] = s;
+        for (int r = threadIdx.x; r < rows; r += THREADS) {
+            double wv = a.w[c0 + r];
+            float2 sv;
+            if constexpr (ARITH == ARITH_DF32) split_f64(wv, sv.x, sv.y);
+            else sv = *reinterpret_cast<float2*>(&wv);
+            ws[ws_idx<E>(r)] = sv;
         }
         __syncthreads();
+        const int nsteps = rows / (4 * E);
 #pragma unroll
         for (int pi = 0; pi < MAXP; pi++) {
             const int p = warp + 8 * pi;
@@ -155,28 +167,37 @@ __global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
             const int cg = p % ncg, ph = p / ncg;
             const int col = cg * 8 + (lane & 7);
             if (col >= ncols) continue;
-            const unsigned char* cp = a.V + (long long)col * a.ldb + r0 * BS;
+            const unsigned char* cp = a.V + (long long)col * a.ldb + c0 * BS;
             float S = 0.f, C = 0.f;
             double D = 0.0;
-#pragma unroll 4
-            for (int s = ph; s < STEPS; s += nph) {
-                const int row = s * 4 * E + sub * E;
-                uint4 raw = ldg_stream(cp + (long long)row * BS);
-                Chunk<FMT> ch;
-                decode_chunk<FMT>(raw, ch);
-                const float2* wp = ws + ws_idx<E>(row);
+            for (int s0 = ph; s0 < nsteps; s0 += U * nph) {
+                uint4 raw[U];
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    float2 wv = wp[e];
-                    if constexpr (ARITH == ARITH_DF32) {
-                        if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
-                        else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
-                    } else {
-                        double wd = *reinterpret_cast<const double*>(&wv);
-                        D = __fma_rn(chunk_f64<FMT>(raw, ch, e), wd, D);
-                    }
+                for (int q = 0; q < U; q++) {
+                    const int st = s0 + q * nph;
+                    raw[q] = st < nsteps ? ldg_stream(cp + (long long)(st * 4 * E + sub * E) * BS)
+                                         : make_uint4(0u, 0u, 0u, 0u);
                 }
-                if constexpr (ARITH == ARITH_DF32) df_renorm(S, C);
+#pragma unroll
+                for (int q = 0; q < U; q++) {
+                    const int st = s0 + q * nph;
+                    if (st >= nsteps) break;
+                    Chunk<FMT> ch;
+                    decode_chunk<FMT>(raw[q], ch);
+                    const float2* wp = ws + ws_idx<E>(st * 4 * E + sub * E);
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        float2 wv = wp[e];
+                        if constexpr (ARITH == ARITH_DF32) {
+                            if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
+                            else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
+                        } else {
+                            double wd = *reinterpret_cast<const double*>(&wv);
+                            D = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), wd, D);
+                        }
+                    }
+                    if constexpr (ARITH == ARITH_DF32) df_renorm(S, C);
+                }
             }
             if constexpr (ARITH == ARITH_DF32) df_add(aS[pi], aC[pi], S, C);
             else aD[pi] += D;
@@ -185,7 +206,7 @@ __global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
 
     // ---- block reduction: red[p][lane] -> per column, then across blocks
     __syncthreads();
-    float2* red = ws;   // reuse (needs npairs*32 <= DOT_TR entries: npairs <= 32)
+    float2* red = ws;   // npairs * 32 <= 1024 entries
 #pragma unroll
     for (int pi = 0; pi < MAXP; pi++) {
         const int p = warp + 8 * pi;
@@ -219,10 +240,12 @@ __global__ void __launch_bounds__(THREADS) k_basis_dot(DotArgs a)
         a.part[(long long)blockIdx.x * MAXCOLS + col] = tot;
     }
     if (last_block(a.counter)) {
-        for (int col = threadIdx.x; col < ncols; col += THREADS) {
-            double s = 0.0;
-            for (unsigned int b = 0; b < gridDim.x; b++) s += __ldcg(a.part + (long long)b * MAXCOLS + col);
-            a.out[col] = s * a.scales[col];
+        // warp-cooperative, fixed order: lane l adds blocks l, l+32, ...; then a shuffle tree
+        for (int col = warp; col < ncols; col += THREADS / 32) {
+            double sum = 0.0;
+            for (unsigned int b = lane; b < gridDim.x; b += 32) sum += __ldcg(a.part + (long long)b * MAXCOLS + col);
+            sum = warp_sum(sum);
+            if (lane == 0) a.out[col] = sum * a.scales[col];
         }
     }
 }
@@ -254,11 +277,12 @@ struct AxpyArgs {
 };
 
 template <int FMT, int ARITH, int EPI>
-__global__ void __launch_bounds__(THREADS) k_basis_axpy(AxpyArgs a)
+__global__ void __launch_bounds__(THREADS, 2) k_basis_axpy(AxpyArgs a)
 {
     if (a.active && *a.active == 0) return;
     constexpr int BS = FmtInfo<FMT>::bytes;
     constexpr int E = 16 / BS;
+    constexpr int U = E <= 8 ? 8 : 4;   // columns (16-byte loads) in flight per thread
     __shared__ float2 cs[MAXCOLS];
     __shared__ double red_s[THREADS / 32], red_m[THREADS / 32];
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
@@ -283,12 +307,12 @@ __global__ void __launch_bounds__(THREADS) k_basis_axpy(AxpyArgs a)
 #pragma unroll
         for (int e = 0; e < E; e++) { S[e] = 0.f; C[e] = 0.f; D[e] = 0.0; }
         int k = 0;
-        for (; k + 4 <= ncols; k += 4) {
-            uint4 raw[4];
+        for (; k + U <= ncols; k += U) {
+            uint4 raw[U];
 #pragma unroll
-            for (int q = 0; q < 4; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
+            for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
+            for (int q = 0; q < U; q++) {
                 Chunk<FMT> ch;
                 decode_chunk<FMT>(raw[q], ch);
                 float2 c = cs[k + q];
@@ -302,10 +326,12 @@ __global__ void __launch_bounds__(THREADS) k_basis_axpy(AxpyArgs a)
                         D[e] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), cd, D[e]);
                     }
                 }
-            }
-            if constexpr (ARITH == ARITH_DF32) {
+                if constexpr (ARITH == ARITH_DF32) {
+                    if ((q & 3) == 3) {
 #pragma unroll
-                for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+                        for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+                    }
+                }
             }
         }
         for (; k < ncols; k++) {
@@ -404,57 +430,70 @@ __device__ __forceinline__ void reduce_norm_parts(const double* part, int np, do
     mx = warp_max(m);
 }
 
-static __device__ void arnoldi_finalize(const StoreArgs& a, double hn)
+// Executed by warp 0 of block 0.  The column, the previous rotations and the
+// coefficients are staged in shared memory by the whole warp first, so lane 0's
+// sequential rotation chain runs at shared-memory latency.
+static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* sR, double* scs, double* ssn)
 {
-    // executed by thread 0 of block 0
     DevState* st = a.d.st;
     const int j = a.j, ldh = st->m + 1;
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i <= j + 1; i += 32) {
+        double hv = 0.0;
+        if (i <= j) {
+            hv = __ldcg(a.d.h + i);
+            if (a.reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
+        } else {
+            hv = hn;
+        }
+        sR[i] = hv;
+        if (i < j) { scs[i] = a.d.cs[i]; ssn[i] = a.d.sn[i]; }
+    }
+    __syncwarp();
     double* Hc = a.d.H + (long long)j * ldh;
+    for (int i = lane; i < ldh; i += 32) Hc[i] = i <= j + 1 ? sR[i] : 0.0;   // raw column
+    __syncwarp();
+    if (lane == 0) {
+        double r0 = sR[0];
+        for (int i = 0; i < j; i++) {
+            const double c = scs[i], s = ssn[i], r1 = sR[i + 1];
+            sR[i] = __dadd_rn(__dmul_rn(c, r0), __dmul_rn(s, r1));
+            r0 = __dadd_rn(__dmul_rn(-s, r0), __dmul_rn(c, r1));
+        }
+        sR[j] = r0;
+        double rr = hypot(r0, hn);
+        double c, s;
+        if (rr == 0.0) { c = 1.0; s = 0.0; }
+        else { c = r0 / rr; s = hn / rr; }
+        a.d.cs[j] = c;
+        a.d.sn[j] = s;
+        sR[j] = rr;
+        sR[j + 1] = 0.0;
+        double gj = a.d.g[j];
+        double gn = __dmul_rn(-s, gj);
+        a.d.g[j + 1] = gn;
+        a.d.g[j] = __dmul_rn(c, gj);
+        double est = fabs(gn);
+        st->est = est;
+        st->hn = hn;
+        st->k = j + 1;
+        st->iters += 1;
+        if (a.reorth) st->reorths += 1;
+        if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
+        int stop = 0;
+        if (!isfinite(hn) || !isfinite(st->omega) || !isfinite(est)) stop = 3;
+        else if (!(hn > st->eps_bd * st->omega)) stop = 2;
+        else if (est <= st->target) stop = 1;
+        else if (j + 1 >= st->kcap) stop = 4;
+        if (stop) {
+            st->stop = stop;
+            st->active = 0;
+            if (a.d.flag_host) *(volatile int*)a.d.flag_host = 0;
+        }
+    }
+    __syncwarp();
     double* Rc = a.d.R + (long long)j * ldh;
-    for (int i = 0; i <= j; i++) {
-        double hv = __ldcg(a.d.h + i);
-        if (a.reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
-        Hc[i] = hv;
-        Rc[i] = hv;
-    }
-    Hc[j + 1] = hn;
-    Rc[j + 1] = hn;
-    for (int i = j + 2; i < ldh; i++) { Hc[i] = 0.0; Rc[i] = 0.0; }
-    for (int i = 0; i < j; i++) {
-        double c = a.d.cs[i], s = a.d.sn[i];
-        double t0 = __dadd_rn(__dmul_rn(c, Rc[i]), __dmul_rn(s, Rc[i + 1]));
-        double t1 = __dadd_rn(__dmul_rn(-s, Rc[i]), __dmul_rn(c, Rc[i + 1]));
-        Rc[i] = t0;
-        Rc[i + 1] = t1;
-    }
-    double rr = hypot(Rc[j], Rc[j + 1]);
-    double c, s;
-    if (rr == 0.0) { c = 1.0; s = 0.0; }
-    else { c = Rc[j] / rr; s = Rc[j + 1] / rr; }
-    a.d.cs[j] = c;
-    a.d.sn[j] = s;
-    Rc[j] = rr;
-    Rc[j + 1] = 0.0;
-    double gj = a.d.g[j];
-    a.d.g[j + 1] = __dmul_rn(-s, gj);
-    a.d.g[j] = __dmul_rn(c, gj);
-    double est = fabs(a.d.g[j + 1]);
-    st->est = est;
-    st->hn = hn;
-    st->k = j + 1;
-    st->iters += 1;
-    if (a.reorth) st->reorths += 1;
-    if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
-    int stop = 0;
-    if (!isfinite(hn) || !isfinite(st->omega) || !isfinite(est)) stop = 3;
-    else if (!(hn > st->eps_bd * st->omega)) stop = 2;
-    else if (est <= st->target) stop = 1;
-    else if (j + 1 >= st->kcap) stop = 4;
-    if (stop) {
-        st->stop = stop;
-        st->active = 0;
-        if (a.d.flag_host) *(volatile int*)a.d.flag_host = 0;
-    }
+    for (int i = lane; i < ldh; i += 32) Rc[i] = i <= j + 1 ? sR[i] : 0.0;
 }
 
 template <int FMT>
@@ -464,6 +503,7 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
     if (st->active == 0) return;
     __shared__ double sh_inv, sh_hn;
     __shared__ EncParams sh_ep;
+    __shared__ double sR[MAXCOLS + 1], scs[MAXCOLS], ssn[MAXCOLS];
     if (threadIdx.x < 32) {
         double ss, mx;
         reduce_norm_parts(a.part_norm, a.nparts, ss, mx);
@@ -482,9 +522,9 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
     __syncthreads();
     const double inv = sh_inv;
     const EncParams ep = sh_ep;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.d.scales[a.col] = ep.scale;
-        if (a.mode == 0) arnoldi_finalize(a, sh_hn);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        if (threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
+        if (a.mode == 0) arnoldi_finalize(a, sh_hn, sR, scs, ssn);
     }
     const long long stride = (long long)gridDim.x * THREADS;
     for (long long i = (long long)blockIdx.x * THREADS + threadIdx.x; i < a.n; i += stride) {

@@ -112,32 +112,6 @@ __global__ void k_scale_columns(const int* col, const double* val, const double*
         out[p] = __dmul_rn(val[p], dinv[col[p]]);
 }
 
-// ||v||_2 and finiteness of a vector; one block, fixed reduction order
-__global__ void k_norm_check(const double* v, long long n, double* out /* [2]: norm, finite */)
-{
-    __shared__ double red[THREADS / 32];
-    __shared__ int fin;
-    if (threadIdx.x == 0) fin = 1;
-    __syncthreads();
-    double s = 0.0;
-    int ok = 1;
-    for (long long i = threadIdx.x; i < n; i += THREADS) {
-        double x = v[i];
-        if (!isfinite(x)) ok = 0;
-        s = __fma_rn(x, x, s);
-    }
-    if (!ok) fin = 0;
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < THREADS / 32; w++) t += red[w];
-        out[0] = sqrt(t);
-        out[1] = fin;
-    }
-}
-
 __global__ void k_init_state(DevState* st, double bnorm, double target, double eps_bd, int m, int record,
                              long long hist_cap)
 {
@@ -180,20 +154,91 @@ __global__ void k_cycle_start(DevArrays d, long long maxit, int m)
     d.g[0] = beta;
 }
 
-// y = R^{-1} g on the k x k upper triangle (Fig. 1 step 17); one warp.
+// y = R^{-1} g on the k x k upper triangle (Fig. 1 step 17); one warp, column-oriented:
+// y_c = g_c / R_cc, then g_i -= R_ic y_c for i < c (lanes split i; column c is
+// contiguous).  The next column is prefetched while the current one is applied.
 __global__ void k_backsolve(DevArrays d)
 {
+    __shared__ double gs[MAXCOLS + 1];
     DevState* st = d.st;
     const int k = st->k, ldh = st->m + 1;
     const int lane = threadIdx.x;
-    for (int i = k - 1; i >= 0; i--) {
-        double s = 0.0;
-        for (int c = i + 1 + lane; c < k; c += 32) s = __fma_rn(d.R[i + (long long)c * ldh], d.y[c], s);
-        s = warp_sum(s);
-        if (lane == 0) d.y[i] = (d.g[i] - s) / d.R[i + (long long)i * ldh];
-        __syncwarp();
+    for (int i = lane; i <= st->m; i += 32) gs[i] = i < k ? d.g[i] : 0.0;
+    __syncwarp();
+    constexpr int PER = (MAXCOLS + 31) / 32;
+    double cur[PER], nxt[PER];
+    if (k > 0) {
+        const double* col = d.R + (long long)(k - 1) * ldh;
+#pragma unroll
+        for (int t = 0; t < PER; t++) { int i = lane + 32 * t; cur[t] = i < k ? col[i] : 0.0; }
     }
-    for (int i = k + lane; i <= st->m; i += 32) d.y[i] = 0.0;
+    for (int c = k - 1; c >= 0; c--) {
+        if (c > 0) {
+            const double* col = d.R + (long long)(c - 1) * ldh;
+#pragma unroll
+            for (int t = 0; t < PER; t++) { int i = lane + 32 * t; nxt[t] = i < c ? col[i] : 0.0; }
+        }
+        // R_cc sits in lane c % 32, slot c / 32
+        double rcc = 0.0;
+#pragma unroll
+        for (int t = 0; t < PER; t++) if (t == c / 32) rcc = cur[t];
+        rcc = __shfl_sync(0xFFFFFFFFu, rcc, c % 32);
+        const double yc = gs[c] / rcc;
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            int i = lane + 32 * t;
+            if (i < c) gs[i] = __dsub_rn(gs[i], __dmul_rn(cur[t], yc));
+        }
+        if (lane == 0) gs[c] = yc;
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < PER; t++) cur[t] = nxt[t];
+    }
+    for (int i = lane; i <= st->m; i += 32) d.y[i] = i < k ? gs[i] : 0.0;
+}
+
+// ||v||_2 and finiteness of a vector: per-block partials, last block combines them in a
+// fixed order.  out[0] = norm, out[1] = 1 if all entries are finite.
+__global__ void __launch_bounds__(THREADS) k_vec_norm(const double* v, long long n, double* part,
+                                                      unsigned int* counter, double* out)
+{
+    __shared__ double red[THREADS / 32];
+    __shared__ int fin;
+    if (threadIdx.x == 0) fin = 1;
+    __syncthreads();
+    double s = 0.0;
+    int ok = 1;
+    for (long long i = (long long)blockIdx.x * THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * THREADS) {
+        double x = v[i];
+        if (!isfinite(x)) ok = 0;
+        s = __fma_rn(x, x, s);
+    }
+    if (!ok) fin = 0;
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < THREADS / 32; w++) t += red[w];
+        part[2 * blockIdx.x] = t;
+        part[2 * blockIdx.x + 1] = fin;
+    }
+    if (last_block(counter)) {
+        if (threadIdx.x < 32) {
+            double t = 0.0, f = 1.0;
+            for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32) {
+                t += __ldcg(part + 2 * b);
+                f = fmin(f, __ldcg(part + 2 * b + 1));
+            }
+            t = warp_sum(t);
+            for (int o = 16; o > 0; o >>= 1) f = fmin(f, __shfl_xor_sync(0xFFFFFFFFu, f, o));
+            if (threadIdx.x == 0) {
+                out[0] = sqrt(t);
+                out[1] = f;
+            }
+        }
+    }
 }
 
 }  // namespace
@@ -504,8 +549,12 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
     CBG_CUDA(cudaEventRecord(h->ev0, s));
     // ||b|| and finiteness of b and x0
     const long long launches0 = h->launches;
-    launch(h, 4, 0.0, [&] { k_norm_check<<<1, THREADS, 0, s>>>(b, h->n, h->scratch); });
-    launch(h, 4, 0.0, [&] { k_norm_check<<<1, THREADS, 0, s>>>(x, h->n, h->scratch + 2); });
+    launch(h, 4, 0.0, [&] {
+        k_vec_norm<<<h->grid_spmv, THREADS, 0, s>>>(b, h->n, h->d.part_spmv, h->d.counters + 4, h->scratch);
+    });
+    launch(h, 4, 0.0, [&] {
+        k_vec_norm<<<h->grid_spmv, THREADS, 0, s>>>(x, h->n, h->d.part_spmv, h->d.counters + 4, h->scratch + 2);
+    });
     double nb[4];
     CBG_CUDA(cudaMemcpyAsync(nb, h->scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CBG_CUDA(cudaStreamSynchronize(s));
@@ -719,8 +768,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     const int occ_dot = std::max(1, op.occ_dot());
     const int occ_axpy = std::max(1, op.occ_axpy());
     const int occ_spmv = std::max(1, spmv_occupancy());
-    const long long dot_tiles = h->ld / DOT_TR;
-    h->grid_dot = (int)std::min<long long>(dot_tiles, (long long)sms * occ_dot);
+    h->grid_dot = (int)std::min<long long>(h->ld / DOT_MIN_ROWS, (long long)sms * occ_dot);
     const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
     h->grid_axpy = (int)std::min<long long>(axpy_blocks, (long long)sms * occ_axpy);
     h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
@@ -934,7 +982,7 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
         return CBG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const Ops& op = ops_for(fmt);
-    int grid = (int)std::min<long long>(ld / DOT_TR, (long long)num_sms() * std::max(1, op.occ_dot()));
+    int grid = (int)std::min<long long>(ld / DOT_MIN_ROWS, (long long)num_sms() * std::max(1, op.occ_dot()));
     double *part = nullptr, *sc = nullptr, *out = nullptr;
     unsigned int* cnt = nullptr;
     int rc = dalloc(&part, (size_t)grid * MAXCOLS);
