@@ -198,6 +198,23 @@ int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int6
  * *out; reset != 0 clears it afterwards.  Errors: CBG_ERR_ARG. */
 int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset);
 
+/* Same computation and arguments as cbg_basis_dot, without allocating device memory.
+ * No counterpart in the paper.  cbg_basis_dot obtains its scratch (per-block partial
+ * sums, a completion counter, device copies of scales and result) from cudaMalloc and
+ * returns it with cudaFree on every call; callers whose device memory is owned by
+ * another allocator (a framework's caching allocator, a fixed pool) cannot count on a
+ * private cudaMalloc succeeding, and callers in latency-critical loops cannot accept the
+ * device-wide synchronisation of cudaFree.  This variant keeps its scratch in one
+ * file-scope device array of about 612 KiB that every GPU loading the library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or allocating routine.
+ * Limits: ncols <= 256 (larger: CBG_ERR_ARG); the kernel uses at most 304 thread blocks.
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the one
+ * array, so calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Synchronises `stream`. */
+int cbg_basis_dot_noalloc(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
+                          const double* scales, const double* w, double* h, void* stream);
+
 /* y = A x with the library's SpMV (device x, y).  For parity checks. */
 int cbgmres_spmv(cbg_handle* h, const double* x, double* y);
 

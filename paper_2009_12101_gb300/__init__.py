@@ -101,6 +101,7 @@ def lib():
             L.cbg_decode.argtypes = [i32, i64, vp, d, vp, vp]
             L.cbg_basis_dot.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
             L.cbg_basis_axpy.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.cbg_basis_dot_noalloc.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
             L.cbgmres_create_batched.argtypes = [i32, vp, i32, i32, C.POINTER(Options), C.POINTER(vp)]
             L.cbgmres_solve_batched.argtypes = [vp, vp, vp, d, i64, vp]
             L.cbgmres_destroy_batched.argtypes = [vp]
@@ -306,6 +307,18 @@ def basis_dot(fmt: str, arith: str, n: int, V, ld: int, scales, w, stream=None) 
     _check(lib().cbg_basis_dot(FORMATS[fmt], ARITH[arith], n, ncols, C.c_void_p(V.data_ptr()), ld,
                                C.c_void_p(sc.ctypes.data), _dev_f64(w), C.c_void_p(h.ctypes.data),
                                _stream_ptr(stream)), "cbg_basis_dot")
+    return h
+
+
+def basis_dot_noalloc(fmt: str, arith: str, n: int, V, ld: int, scales, w, stream=None) -> np.ndarray:
+    """h = V^T w like basis_dot, through the entry point that allocates no device memory
+    (its scratch is a static device array shared by all calls; see cbgmres.h)."""
+    ncols = V.shape[0]
+    h = np.zeros(ncols)
+    sc = np.ascontiguousarray(scales, np.float64)
+    _check(lib().cbg_basis_dot_noalloc(FORMATS[fmt], ARITH[arith], n, ncols, C.c_void_p(V.data_ptr()), ld,
+                                       C.c_void_p(sc.ctypes.data), _dev_f64(w), C.c_void_p(h.ctypes.data),
+                                       _stream_ptr(stream)), "cbg_basis_dot_noalloc")
     return h
 
 
