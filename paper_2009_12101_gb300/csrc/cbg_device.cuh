@@ -203,22 +203,41 @@ template <int FMT> __device__ __forceinline__ void decode_chunk(const uint4& raw
     }
 }
 
+// Exact FP32 -> FP64 conversion with integer operations (the F2F instruction runs on
+// GB300's slow FP64 pipe).  Normal numbers and zeros take the integer path; subnormal,
+// infinite and NaN inputs fall back to the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e - 1u < 254u) {
+        const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+        const unsigned int lo = (u & 7u) << 29;
+        return __hiloint2double((int)hi, (int)lo);
+    }
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
 // Exact FP64 value of one code (scale not applied); used by the FP64 arithmetic mode,
 // the SpMV and the decode kernel.
 template <int FMT> __device__ __forceinline__ double code_value(const void* base, int64_t i)
 {
     if constexpr (FMT == F64) return reinterpret_cast<const double*>(base)[i];
-    else if constexpr (FMT == F32) return (double)reinterpret_cast<const float*>(base)[i];
-    else if constexpr (FMT == F16) return (double)__half2float(reinterpret_cast<const __half*>(base)[i]);
+    else if constexpr (FMT == F32) return f32_to_f64_exact(reinterpret_cast<const float*>(base)[i]);
+    else if constexpr (FMT == F16) return f32_to_f64_exact(__half2float(reinterpret_cast<const __half*>(base)[i]));
     else if constexpr (FMT == BF16)
-        return (double)__uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(base)[i]) << 16);
+        return f32_to_f64_exact(__uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(base)[i]) << 16));
     else if constexpr (FMT == E4M3) {
         unsigned int c = reinterpret_cast<const unsigned char*>(base)[i];
         float a, b;
         dec_e4m3x2(c, a, b);
-        return (double)a;
-    } else if constexpr (FMT == I32) return (double)reinterpret_cast<const int*>(base)[i];
-    else return (double)reinterpret_cast<const short*>(base)[i];
+        return f32_to_f64_exact(a);
+    } else if constexpr (FMT == I32) {
+        float hi, lo;
+        dec_i32(reinterpret_cast<const int*>(base)[i], hi, lo);   // both parts exact
+        return __dadd_rn(f32_to_f64_exact(hi), f32_to_f64_exact(lo));
+    } else return f32_to_f64_exact(dec_i16((int)reinterpret_cast<const short*>(base)[i]));
 }
 
 // ------------------------------------------------------------------------- encoding

@@ -38,6 +38,7 @@ struct DevState {
     long long hist_cap;
     int last_k;           // columns of the previous cycle (set when a cycle starts)
     int pad0;
+    double wnorm, wmax;   // ||w||_2 and ||w||_inf of the orthogonalised w (last axpy block)
 };
 
 // per-handle arrays addressed by the kernels
@@ -78,6 +79,16 @@ __device__ __forceinline__ bool last_block(unsigned int* counter)
     return is_last;
 }
 
+__device__ __forceinline__ void reduce_norm_parts(const double* part, int np, double& ss, double& mx)
+{
+    // fixed order: lane l sums parts l, l+32, ...; then a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    double s = 0.0, m = 0.0;
+    for (int p = lane; p < np; p += 32) { s += __ldcg(part + 2 * p); m = fmax(m, __ldcg(part + 2 * p + 1)); }
+    ss = warp_sum(s);
+    mx = warp_max(m);
+}
+
 // FP64 value of element e of a decoded chunk (scale not applied); exact for every format
 template <int FMT>
 __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& ch, int e)
@@ -86,9 +97,9 @@ __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& 
         const unsigned int w[4] = {raw.x, raw.y, raw.z, raw.w};
         return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
     } else if constexpr (SingleFloat<FMT>::value) {
-        return (double)ch.vh[e];
+        return f32_to_f64_exact(ch.vh[e]);
     } else {
-        return __dadd_rn((double)ch.vh[e], (double)ch.vl[e]);
+        return __dadd_rn(f32_to_f64_exact(ch.vh[e]), f32_to_f64_exact(ch.vl[e]));
     }
 }
 
@@ -99,6 +110,7 @@ __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& 
 constexpr int DOT_ROWS = 4096;
 template <int E> __device__ __forceinline__ int ws_idx(int r) { return E >= 8 ? r + 2 * (r / E) : r; }
 template <int E> struct WsLen { static constexpr int value = E >= 8 ? DOT_ROWS + DOT_ROWS / 4 : DOT_ROWS; };
+
 
 // ============================================================== h = V^T w  (steps 5, 8)
 // Lane-per-column schedule: lane l of a warp owns column 8*cg + (l & 7) and row
@@ -122,66 +134,101 @@ struct DotArgs {
     const int* active;        // skip when *active == 0 (may be null)
 };
 
+// Work items of the dot kernel: column group cg (8 columns) x row phase ph (the ph-th
+// of nph contiguous segments of the chunk's steps).  nph in {1, 2, 4, 8} is the smallest that spreads the items
+// evenly over the 8 warps (at most 64 items, so their accumulators fit in shared memory).
+__device__ __forceinline__ int dot_phases(int ncg)
+{
+    int best = 1, best_load = 1 << 30;
+    for (int nph = 1; nph <= 8; nph *= 2) {
+        const int items = ncg * nph;
+        if (items > 64) break;
+        const int load = ((items + 7) / 8) * 64 / nph;          // busiest warp, in 1/64 chunk units
+        if (load < best_load) { best_load = load; best = nph; }
+    }
+    return best;
+}
+
+constexpr int DOT_MAXITEMS = 64;
+// dynamic shared memory of k_basis_dot: staged w, then per-(item, lane) accumulators
+template <int FMT> constexpr int dot_smem_bytes()
+{
+    return (WsLen<16 / FmtInfo<FMT>::bytes>::value + DOT_MAXITEMS * 32) * (int)sizeof(float2);
+}
+
 template <int FMT, int ARITH>
-__global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
+__global__ void __launch_bounds__(THREADS, 3) k_basis_dot(DotArgs a)
 {
     if (a.active && *a.active == 0) return;
     constexpr int BS = FmtInfo<FMT>::bytes;
     constexpr int E = 16 / BS;
-    constexpr int MAXP = 4;                        // pairs per warp (MAXCOLS / 8 / 8)
     constexpr int U = 8;                           // loads in flight per lane
-    __shared__ __align__(16) float2 ws[WsLen<E>::value];
+    extern __shared__ __align__(16) float2 dot_smem[];
+    float2* ws = dot_smem;                               // staged w (padded layout)
+    float2* acc = dot_smem + WsLen<E>::value;            // per (item, lane), owned by one warp
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ncg = (ncols + 7) >> 3;
-    const int nph = ncg >= 8 ? 1 : 8 / ncg;
-    const int npairs = ncg * nph;
+    const int nph = dot_phases(ncg);
+    const int nitems = ncg * nph;
     const int sub = lane >> 3;
+
+    for (int i = threadIdx.x; i < nitems * 32; i += THREADS) acc[i] = make_float2(0.f, 0.f);
 
     // contiguous row range of this block (multiples of 64 rows)
     const long long per = ((a.nrows + gridDim.x - 1) / gridDim.x + 63) / 64 * 64;
     const long long rb = (long long)blockIdx.x * per;
     const long long re = rb + per < a.nrows ? rb + per : a.nrows;
 
-    float aS[MAXP], aC[MAXP];
-    double aD[MAXP];
-#pragma unroll
-    for (int p = 0; p < MAXP; p++) { aS[p] = 0.f; aC[p] = 0.f; aD[p] = 0.0; }
-
     for (long long c0 = rb; c0 < re; c0 += DOT_ROWS) {
         const int rows = (int)(re - c0 < DOT_ROWS ? re - c0 : DOT_ROWS);
         __syncthreads();
-        for (int r = threadIdx.x; r < rows; r += THREADS) {
-            double wv = a.w[c0 + r];
-            float2 sv;
-            if constexpr (ARITH == ARITH_DF32) split_f64(wv, sv.x, sv.y);
-            else sv = *reinterpret_cast<float2*>(&wv);
-            ws[ws_idx<E>(r)] = sv;
+        {   // all of this thread's w loads in flight at once, then split into shared memory
+            constexpr int PER = DOT_ROWS / THREADS;
+            double wb[PER];
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                const int r = threadIdx.x + q * THREADS;
+                wb[q] = r < rows ? __ldcg(a.w + c0 + r) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                const int r = threadIdx.x + q * THREADS;
+                if (r < rows) {
+                    float2 sv;
+                    if constexpr (ARITH == ARITH_DF32) split_f64(wb[q], sv.x, sv.y);
+                    else sv = *reinterpret_cast<float2*>(&wb[q]);
+                    ws[ws_idx<E>(r)] = sv;
+                }
+            }
         }
         __syncthreads();
         const int nsteps = rows / (4 * E);
-#pragma unroll
-        for (int pi = 0; pi < MAXP; pi++) {
-            const int p = warp + 8 * pi;
-            if (p >= npairs) break;
-            const int cg = p % ncg, ph = p / ncg;
+        for (int it = warp; it < nitems; it += THREADS / 32) {
+            const int cg = it % ncg, ph = it / ncg;
             const int col = cg * 8 + (lane & 7);
             if (col >= ncols) continue;
             const unsigned char* cp = a.V + (long long)col * a.ldb + c0 * BS;
             float S = 0.f, C = 0.f;
             double D = 0.0;
-            for (int s0 = ph; s0 < nsteps; s0 += U * nph) {
+            // phase ph streams a contiguous segment of steps, so each warp consumes whole
+            // cache lines of its columns (interleaving phases would split a line between
+            // warps running at different times and fetch it twice)
+            const int seg = (nsteps + nph - 1) / nph;
+            const int s_beg = ph * seg;
+            const int s_end = s_beg + seg < nsteps ? s_beg + seg : nsteps;
+            for (int s0 = s_beg; s0 < s_end; s0 += U) {
                 uint4 raw[U];
 #pragma unroll
                 for (int q = 0; q < U; q++) {
-                    const int st = s0 + q * nph;
-                    raw[q] = st < nsteps ? ldg_stream(cp + (long long)(st * 4 * E + sub * E) * BS)
-                                         : make_uint4(0u, 0u, 0u, 0u);
+                    const int st = s0 + q;
+                    raw[q] = st < s_end ? ldg_stream(cp + (long long)(st * 4 * E + sub * E) * BS)
+                                        : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
                 for (int q = 0; q < U; q++) {
-                    const int st = s0 + q * nph;
-                    if (st >= nsteps) break;
+                    const int st = s0 + q;
+                    if (st >= s_end) break;
                     Chunk<FMT> ch;
                     decode_chunk<FMT>(raw[q], ch);
                     const float2* wp = ws + ws_idx<E>(st * 4 * E + sub * E);
@@ -199,24 +246,20 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
                     if constexpr (ARITH == ARITH_DF32) df_renorm(S, C);
                 }
             }
-            if constexpr (ARITH == ARITH_DF32) df_add(aS[pi], aC[pi], S, C);
-            else aD[pi] += D;
+            float2& slot = acc[it * 32 + lane];
+            if constexpr (ARITH == ARITH_DF32) {
+                float2 v = slot;
+                df_add(v.x, v.y, S, C);
+                slot = v;
+            } else {
+                double v = *reinterpret_cast<double*>(&slot);
+                v += D;
+                slot = *reinterpret_cast<float2*>(&v);
+            }
         }
     }
 
-    // ---- block reduction: red[p][lane] -> per column, then across blocks
-    __syncthreads();
-    float2* red = ws;   // npairs * 32 <= 1024 entries
-#pragma unroll
-    for (int pi = 0; pi < MAXP; pi++) {
-        const int p = warp + 8 * pi;
-        if (p < npairs) {
-            float2 v;
-            if constexpr (ARITH == ARITH_DF32) v = make_float2(aS[pi], aC[pi]);
-            else v = *reinterpret_cast<float2*>(&aD[pi]);
-            red[p * 32 + lane] = v;
-        }
-    }
+    // ---- block reduction: per column over its phases and row subgroups, then blocks
     __syncthreads();
     for (int col = threadIdx.x; col < ncols; col += THREADS) {
         const int cg = col >> 3, c8 = col & 7;
@@ -225,7 +268,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
             float S = 0.f, C = 0.f;
             for (int ph = 0; ph < nph; ph++)
                 for (int sb = 0; sb < 4; sb++) {
-                    float2 v = red[(ph * ncg + cg) * 32 + sb * 8 + c8];
+                    float2 v = acc[(ph * ncg + cg) * 32 + sb * 8 + c8];
                     df_add(S, C, v.x, v.y);
                 }
             tot = df_to_double(S, C);
@@ -233,7 +276,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
             tot = 0.0;
             for (int ph = 0; ph < nph; ph++)
                 for (int sb = 0; sb < 4; sb++) {
-                    float2 v = red[(ph * ncg + cg) * 32 + sb * 8 + c8];
+                    float2 v = acc[(ph * ncg + cg) * 32 + sb * 8 + c8];
                     tot += *reinterpret_cast<double*>(&v);
                 }
         }
@@ -274,6 +317,8 @@ struct AxpyArgs {
     long long n;              // true rows (norms exclude padding)
     double* part_norm;        // [gridDim.x][2]
     const int* active;
+    unsigned int* counter;    // EPI_SUB final pass: last block writes st->wnorm, st->wmax
+    DevState* st;
 };
 
 template <int FMT, int ARITH, int EPI>
@@ -395,6 +440,16 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_axpy(AxpyArgs a)
             a.part_norm[2 * blockIdx.x] = s;
             a.part_norm[2 * blockIdx.x + 1] = m;
         }
+        if (a.counter) {
+            if (last_block(a.counter) && threadIdx.x < 32) {
+                double s2, m2;
+                reduce_norm_parts(a.part_norm, gridDim.x, s2, m2);
+                if (threadIdx.x == 0) {
+                    a.st->wnorm = sqrt(s2);
+                    a.st->wmax = m2;
+                }
+            }
+        }
     }
 }
 
@@ -414,21 +469,10 @@ struct StoreArgs {
     int j;                    // Hessenberg column being completed (mode 0)
     int mode;
     int reorth;               // pass 2 ran (h += u)
-    const double* part_norm;  // per-block (sumsq, max) from the producer
-    int nparts;
     long long n;
     int fmt;
 };
 
-__device__ __forceinline__ void reduce_norm_parts(const double* part, int np, double& ss, double& mx)
-{
-    // fixed order: lane l sums parts l, l+32, ...; then a fixed shuffle tree
-    const int lane = threadIdx.x & 31;
-    double s = 0.0, m = 0.0;
-    for (int p = lane; p < np; p += 32) { s += __ldcg(part + 2 * p); m = fmax(m, __ldcg(part + 2 * p + 1)); }
-    ss = warp_sum(s);
-    mx = warp_max(m);
-}
 
 // Executed by warp 0 of block 0.  The column, the previous rotations and the
 // coefficients are staged in shared memory by the whole warp first, so lane 0's
@@ -504,20 +548,15 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
     __shared__ double sh_inv, sh_hn;
     __shared__ EncParams sh_ep;
     __shared__ double sR[MAXCOLS + 1], scs[MAXCOLS], ssn[MAXCOLS];
-    if (threadIdx.x < 32) {
-        double ss, mx;
-        reduce_norm_parts(a.part_norm, a.nparts, ss, mx);
-        if (threadIdx.x == 0) {
-            double hn = sqrt(ss);
-            if (a.mode == 1) {           // first vector: norms of r0 from the residual kernel
-                hn = st->beta;
-                mx = st->rinf;
-            }
-            double inv = 1.0 / hn;
-            sh_hn = hn;
-            sh_inv = inv;
-            sh_ep = enc_params(FMT, __dmul_rn(mx, inv));
-        }
+    if (threadIdx.x == 0) {
+        // norms of the vector to store: the residual (first vector of a cycle) or the
+        // orthogonalised w, both finalised by the last block of the producing kernel
+        const double hn = a.mode == 1 ? st->beta : st->wnorm;
+        const double mx = a.mode == 1 ? st->rinf : st->wmax;
+        const double inv = 1.0 / hn;
+        sh_hn = hn;
+        sh_inv = inv;
+        sh_ep = enc_params(FMT, __dmul_rn(mx, inv));
     }
     __syncthreads();
     const double inv = sh_inv;
@@ -527,9 +566,18 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
         if (a.mode == 0) arnoldi_finalize(a, sh_hn, sR, scs, ssn);
     }
     const long long stride = (long long)gridDim.x * THREADS;
-    for (long long i = (long long)blockIdx.x * THREADS + threadIdx.x; i < a.n; i += stride) {
-        double v = __dmul_rn(a.w[i], inv);
-        encode_store<FMT>(a.Vcol, i, v, ep);
+    for (long long i0 = (long long)blockIdx.x * THREADS + threadIdx.x; i0 < a.n; i0 += 4 * stride) {
+        double wv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {   // four loads in flight per thread
+            const long long i = i0 + q * stride;
+            wv[q] = i < a.n ? __ldcg(a.w + i) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const long long i = i0 + q * stride;
+            if (i < a.n) encode_store<FMT>(a.Vcol, i, __dmul_rn(wv[q], inv), ep);
+        }
     }
 }
 

@@ -453,6 +453,8 @@ void enqueue_step(cbg_handle* h, int j)
     xa.coef = h->d.h;
     xa.w_in = h->w;
     xa.w_out = reorth ? h->w1 : h->w2;
+    xa.st = h->d.st;
+    xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
     launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     if (reorth) {
         // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
@@ -463,6 +465,7 @@ void enqueue_step(cbg_handle* h, int j)
         xa.coef = h->d.u;
         xa.w_in = h->w1;
         xa.w_out = h->w2;
+        xa.counter = h->d.counters + 5;
         launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     }
     // steps 6, 12-14 and the Givens update
@@ -474,8 +477,6 @@ void enqueue_step(cbg_handle* h, int j)
     sa.j = j;
     sa.mode = 0;
     sa.reorth = reorth ? 1 : 0;
-    sa.part_norm = h->d.part_norm;
-    sa.nparts = h->grid_axpy;
     sa.n = h->n;
     sa.fmt = h->fmt;
     launch(h, 3, store_bytes(h), [&] { op.store(h->grid_store, s, sa); });
@@ -490,8 +491,6 @@ void enqueue_first_vector(cbg_handle* h)
     sa.col = 0;
     sa.j = 0;
     sa.mode = 1;
-    sa.part_norm = h->d.part_spmv;
-    sa.nparts = 0;
     sa.n = h->n;
     sa.fmt = h->fmt;
     launch(h, 3, store_bytes(h), [&] { ops_for(h->fmt).store(h->grid_store, h->stream, sa); });
@@ -771,7 +770,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->grid_dot = (int)std::min<long long>(h->ld / DOT_MIN_ROWS, (long long)sms * occ_dot);
     const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
     h->grid_axpy = (int)std::min<long long>(axpy_blocks, (long long)sms * occ_axpy);
-    h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
+    h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 8);
     h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
     h->grid_spmv = (int)std::min<long long>((n * h->group + THREADS - 1) / THREADS, (long long)sms * occ_spmv);
     h->grid_dot = std::max(1, h->grid_dot);
