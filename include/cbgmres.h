@@ -132,6 +132,10 @@ void cbgmres_options_default(cbg_options* opt);
 /* Human-readable text of a status code (static storage). */
 const char* cbgmres_status_string(int status);
 
+/* Text of the last CUDA error the library saw on the calling thread (after an entry
+ * point returned CBG_ERR_CUDA); static storage. */
+const char* cbgmres_last_error(void);
+
 /* Bytes per stored basis element of `fmt` (8, 4, 2 or 1), 0 for an invalid format. */
 int cbgmres_format_bytes(int fmt);
 
@@ -219,14 +223,33 @@ int cbg_basis_dot_noalloc(int fmt, int arith, int64_t n, int ncols, const void* 
 int cbgmres_spmv(cbg_handle* h, const double* x, double* y);
 
 /* ---- batched solve (many independent systems, one persistent launch) ---------------
- * nsys systems As[s] (host or device CSR per on_device), all with restart `restart` and
- * format `fmt`.  One persistent kernel runs whole GMRES(m) solves, one thread block per
- * system taken from a device work queue ordered by decreasing size; the launch is
- * replayed from a CUDA graph.  Per-system x (device) holds x0 on entry. */
+ * nsys systems As[s] (host or device CSR per on_device), all with restart length
+ * `restart` (<= 64) and basis format `fmt`; options.precond NONE or JACOBI, reorth ALWAYS,
+ * arith DF32.  One persistent kernel with thread-block clusters runs every GMRES(m)
+ * solve on the device (Fig. 1 with the explicit-residual recheck of Section 5.2): a
+ * device work queue hands out systems in decreasing size; systems with at least
+ * `split_rows` rows are solved by a whole cluster (rows split across its blocks, sums
+ * through distributed shared memory), smaller ones by single blocks.  With
+ * options.use_graph the launch is replayed from a CUDA graph.
+ * Vectors are packed: system s occupies entries [off_s, off_s + n_s) with off_s the sum
+ * of the sizes of systems 0..s-1 (the order of As).  Errors: CBG_ERR_ARG (bad CSR,
+ * restart > 64), CBG_ERR_UNSUPPORTED (other options), CBG_ERR_OOM, CBG_ERR_CUDA. */
 int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt,
                            const cbg_options* opt, cbg_batch** out);
-int cbgmres_solve_batched(cbg_batch* bt, const double* const* b, double* const* x,
-                          double tol, int64_t maxit, cbg_stats* per_sys);
+/* Solve every system: b, x device arrays (packed, total rows); x holds x0 on entry.
+ * per_sys (host, nsys entries, may be NULL) receives iterations, restarts, the explicit
+ * relative residual and the status of each system; ms_total is the batch time.  Returns
+ * the worst status (negative first, then CBG_NOT_CONVERGED).  Synchronises the stream. */
+int cbgmres_solve_batched(cbg_batch* bt, const double* b, double* x, double tol, int64_t maxit,
+                          cbg_stats* per_sys);
+/* Autotuner: time every feasible schedule (cluster size 1..16, split threshold) on this
+ * problem (x restored to x0 before each trial) and keep the fastest; cache_path (may be
+ * NULL) is a JSON-lines file consulted first and appended to, keyed by GPU, format,
+ * restart length, system count and total rows.  The chosen schedule is returned. */
+int cbgmres_tune_batched(cbg_batch* bt, const double* b, double* x, double tol, int64_t maxit,
+                         const char* cache_path, int* cluster_out, int* split_rows_out);
+/* Set the schedule explicitly (cluster size a power of two <= 16). */
+int cbgmres_batched_schedule(cbg_batch* bt, int cluster, int split_rows);
 void cbgmres_destroy_batched(cbg_batch* bt);
 
 #ifdef __cplusplus

@@ -32,7 +32,10 @@ TILE_ROWS = 4096   # padded rows per basis column (multiple of every kernel tile
 
 class CbgError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: status {status} ({STATUS.get(status, '?')})")
+        msg = f"{where}: status {status} ({STATUS.get(status, '?')})"
+        if status == -4 and _lib is not None:
+            msg += f": {_lib.cbgmres_last_error().decode()}"
+        super().__init__(msg)
         self.status = status
 
 
@@ -87,6 +90,8 @@ def lib():
             L.cbgmres_status_string.argtypes = [i32]
             L.cbgmres_status_string.restype = C.c_char_p
             L.cbgmres_format_bytes.argtypes = [i32]
+            L.cbgmres_last_error.argtypes = []
+            L.cbgmres_last_error.restype = C.c_char_p
             L.cbgmres_create.argtypes = [C.POINTER(Csr), i32, i32, C.POINTER(Options), C.POINTER(vp)]
             L.cbgmres_set_spai.argtypes = [vp, vp, i32]
             L.cbgmres_solve.argtypes = [vp, vp, vp, d, i64, C.POINTER(Stats)]
@@ -104,6 +109,9 @@ def lib():
             L.cbg_basis_dot_noalloc.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
             L.cbgmres_create_batched.argtypes = [i32, vp, i32, i32, C.POINTER(Options), C.POINTER(vp)]
             L.cbgmres_solve_batched.argtypes = [vp, vp, vp, d, i64, vp]
+            L.cbgmres_tune_batched.argtypes = [vp, vp, vp, d, i64, C.c_char_p, C.POINTER(C.c_int),
+                                               C.POINTER(C.c_int)]
+            L.cbgmres_batched_schedule.argtypes = [vp, i32, i32]
             L.cbgmres_destroy_batched.argtypes = [vp]
             L.cbgmres_destroy_batched.restype = None
             _lib = L
@@ -331,3 +339,64 @@ def basis_axpy(fmt: str, arith: str, n: int, V, ld: int, scales, h, w, stream=No
                                 C.c_void_p(sc.ctypes.data), C.c_void_p(hh.ctypes.data), _dev_f64(w),
                                 _stream_ptr(stream)), "cbg_basis_axpy")
     return w
+
+
+class BatchedSolver:
+    """Many independent systems solved by one persistent cluster launch.
+
+    mats: list of objects with rowptr/col/val (host numpy) -- e.g. workloads.CSR.
+    Vectors are packed in the order of `mats` (offsets = prefix sums of the sizes)."""
+
+    def __init__(self, mats, *, restart: int = 30, fmt: str = "f32", precond: str = "jacobi",
+                 use_graph: bool = True, stream=None):
+        _torch()
+        self.mats = mats
+        self.sizes = np.array([int(len(A.rowptr) - 1) for A in mats])
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        self.total = int(self.offsets[-1])
+        self._keep = []
+        arr = (Csr * len(mats))()
+        for i, A in enumerate(mats):
+            rp = np.ascontiguousarray(A.rowptr, np.int32); ci = np.ascontiguousarray(A.col, np.int32)
+            va = np.ascontiguousarray(A.val, np.float64)
+            self._keep += [rp, ci, va]
+            arr[i] = Csr(rp.size - 1, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, 0)
+        opt = options(precond=precond, stream=stream)
+        opt.use_graph = int(use_graph)
+        h = C.c_void_p()
+        _check(lib().cbgmres_create_batched(len(mats), C.cast(arr, C.c_void_p), restart, FORMATS[fmt],
+                                            C.byref(opt), C.byref(h)), "cbgmres_create_batched")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cbgmres_destroy_batched(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, b, x, tol: float = 1e-8, maxit: int = 100000) -> dict:
+        st = (Stats * len(self.mats))()
+        rc = lib().cbgmres_solve_batched(self._h, _dev_f64(b, self.total, "b"), _dev_f64(x, self.total, "x"),
+                                         tol, maxit, C.cast(st, C.c_void_p))
+        _check(rc, "cbgmres_solve_batched")
+        return {"status": rc, "ms": st[0].ms_total,
+                "iters": np.array([s.iters for s in st]), "restarts": np.array([s.restarts for s in st]),
+                "relres": np.array([s.true_relres for s in st]), "statuses": np.array([s.status for s in st]),
+                "kernel_launches": st[0].kernel_launches}
+
+    def tune(self, b, x, tol: float = 1e-8, maxit: int = 100000, cache_path: str | None = None):
+        c = C.c_int(); sr = C.c_int()
+        _check(lib().cbgmres_tune_batched(self._h, _dev_f64(b, self.total, "b"), _dev_f64(x, self.total, "x"),
+                                          tol, maxit, cache_path.encode() if cache_path else None,
+                                          C.byref(c), C.byref(sr)), "cbgmres_tune_batched")
+        return c.value, sr.value
+
+    def schedule(self, cluster: int, split_rows: int):
+        _check(lib().cbgmres_batched_schedule(self._h, cluster, split_rows), "cbgmres_batched_schedule")

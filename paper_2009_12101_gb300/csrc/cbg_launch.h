@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "cbg_batched.cuh"
 #include "cbg_kernels.cuh"
 
 namespace cbg {
@@ -19,6 +20,9 @@ template <int FMT> struct Launcher {
                        double* out);
     static int occupancy_dot();
     static int occupancy_axpy();
+    // batched persistent solve with thread-block clusters of `cluster` blocks
+    static cudaError_t batched(int cluster, int grid, size_t smem, cudaStream_t s, const BatchArgs& a);
+    static int batched_max_clusters(int cluster, size_t smem);
 };
 
 // SpMV with an FP64 input vector (residual, SPAI second stage, x += P t)

@@ -92,3 +92,54 @@ template <int FMT> int Launcher<FMT>::occupancy_axpy()
 }
 
 }  // namespace cbg
+
+namespace cbg {
+
+template <int FMT> static void batched_opt_in(size_t smem)
+{
+    cudaFuncSetAttribute(k_batched<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_batched<FMT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+template <int FMT>
+cudaError_t Launcher<FMT>::batched(int cluster, int grid, size_t smem, cudaStream_t s, const BatchArgs& a)
+{
+    batched_opt_in<FMT>(smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batched<FMT>, a);
+}
+
+template <int FMT> int Launcher<FMT>::batched_max_clusters(int cluster, size_t smem)
+{
+    batched_opt_in<FMT>(smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(BT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_batched<FMT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+}  // namespace cbg

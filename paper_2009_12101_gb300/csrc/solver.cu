@@ -243,6 +243,9 @@ __global__ void __launch_bounds__(THREADS) k_vec_norm(const double* v, long long
 
 }  // namespace
 
+// last CUDA error seen by the library on this thread (cbgmres_last_error)
+void cbg_record_cuda_error(cudaError_t e) { last_cuda_error = e; }
+
 // ======================================================================== the handle
 struct cbg_handle {
     long long n = 0, nnz = 0, ld = 0, ldb = 0;
@@ -681,6 +684,11 @@ const char* cbgmres_status_string(int s)
 
 int cbgmres_format_bytes(int fmt) { return fmt_bytes(fmt); }
 
+const char* cbgmres_last_error(void)
+{
+    return last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(last_cuda_error);
+}
+
 int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* opt, cbg_handle** out)
 {
     if (!out) return CBG_ERR_ARG;
@@ -1047,17 +1055,6 @@ int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int6
     return rc;
 }
 
-int cbgmres_create_batched(int, const cbg_csr*, int, int, const cbg_options*, cbg_batch** out)
-{
-    if (out) *out = nullptr;
-    return CBG_ERR_UNSUPPORTED;
-}
 
-int cbgmres_solve_batched(cbg_batch*, const double* const*, double* const*, double, int64_t, cbg_stats*)
-{
-    return CBG_ERR_UNSUPPORTED;
-}
-
-void cbgmres_destroy_batched(cbg_batch*) {}
 
 }  // extern "C"
