@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
+    p.add_argument("--workload", choices=["convdiff128", "batch512"], default="convdiff128")
     return p.parse_args()
 
 
@@ -185,11 +186,128 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------------ batch workload
+BATCH_WORKLOAD = "batch512_stencil2d3d_lognormal0.5_restart30_tol1e-8_jacobi"
+
+
+def batch_model_bytes(mats, iters, restarts, m, bs):
+    """SpMV + 4 basis passes per Arnoldi step, summed over every system's cycles."""
+    tot = 0.0
+    for A, it, rs in zip(mats, iters, restarts):
+        it, rs = int(it), int(rs)
+        spmv = 12.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n
+        last = it - m * max(0, rs - 1)
+        cols = (rs - 1) * m * (m + 1) / 2 + last * (last + 1) / 2 if rs > 0 else 0.0
+        tot += it * spmv + 4.0 * A.n * bs * cols
+    return tot
+
+
+def run_batch(args):
+    import tempfile
+
+    import torch
+    import paper_2009_12101_gb300 as cb
+    import workloads as W
+    cb.ensure_built()
+    mats = W.stencil_batch()
+    xs = [W.exact_solution(A.n, 4, salt=i) for i, A in enumerate(mats)]
+    b = np.concatenate([W.rhs_from_solution(A, x) for A, x in zip(mats, xs)])
+    fmts = ["f64", "f32", "f16"]
+    tol, m = 1e-8, 30
+    stream = torch.cuda.current_stream()
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+    solvers, sched = {}, {}
+    cache = os.path.join(tempfile.gettempdir(), "cbgmres_batch_tune.jsonl")
+    for f in fmts:
+        solvers[f] = cb.BatchedSolver(mats, restart=m, fmt=f, precond="jacobi", use_graph=True)
+        x.zero_()
+        sched[f] = solvers[f].tune(bd, x, tol=tol, cache_path=cache)
+    for _ in range(args.warmup):
+        for f in fmts:
+            x.zero_(); solvers[f].solve(bd, x, tol=tol)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start(); time.sleep(0.3)
+    torch.cuda.synchronize()
+    times = {f: [] for f in fmts}
+    outs = {}
+    launches = 0
+    for _ in range(args.steps):
+        for f in fmts:
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs[f] = solvers[f].solve(bd, x, tol=tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[f].append(e0.elapsed_time(e1))
+            launches += outs[f]["kernel_launches"]
+    clk = clocks.stop()
+    t = {f: sum(v) / len(v) for f, v in times.items()}
+    peak, peak_kind = measured_peaks()
+    o = outs["f32"]
+    mb = batch_model_bytes(mats, o["iters"], o["restarts"], m, 4)
+    achieved = mb / (t["f32"] * 1e-3) / 1e9
+    # the same 512 systems one by one through the single-system solver (f32, Jacobi)
+    seq_ms = None
+    if not args.no_cpu:
+        tot = 0.0
+        for A, bb in zip(mats, np.split(b, np.cumsum([A.n for A in mats])[:-1])):
+            with cb.Solver.from_csr(A, restart=m, fmt="f32", precond="jacobi") as s1:
+                bt = torch.from_numpy(bb).cuda(); xt = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+                s1.solve(bt, xt, tol=tol)   # warm
+                xt.zero_()
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream); s1.solve(bt, xt, tol=tol); e1.record(stream); torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+        seq_ms = tot
+    # end to end: pinned host b -> device, solve, x -> host
+    bh = torch.from_numpy(b).pin_memory(); xh = torch.zeros(b.size, dtype=torch.float64).pin_memory()
+    te = {}
+    for f in ("f64", "f32"):
+        xh.zero_()
+        torch.cuda.synchronize(); t0 = time.perf_counter()
+        bdev = bh.cuda(non_blocking=True); xdev = xh.cuda(non_blocking=True)
+        solvers[f].solve(bdev, xdev, tol=tol)
+        xh.copy_(xdev); torch.cuda.synchronize()
+        te[f] = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": round(t["f64"] / t["f32"], 4), "unit": "x", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "nsys": len(mats), "total_rows": int(b.size), "restart": m,
+                   "tol": tol, "formats": fmts, "schedule_cluster_split": {f: list(v) for f, v in sched.items()},
+                   "l2": "no flush: basis of the batch (0.5-2 GB) exceeds the 129 MB L2"},
+        "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},
+        "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()},
+        "iterations_total": {f: int(outs[f]["iters"].sum()) for f in fmts},
+        "iterations_max": {f: int(outs[f]["iters"].max()) for f in fmts},
+        "status": {f: int(outs[f]["status"]) for f in fmts},
+        "max_relres": {f: float(outs[f]["relres"].max()) for f in fmts},
+        "sequential_single_solver_f32_s": round(seq_ms / 1000, 4) if seq_ms else None,
+        "batching_speedup_f32": round(seq_ms / t["f32"], 2) if seq_ms else None,
+        "roofline": {"bound": "hbm", "kernel": "k_batched (f32)", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "algorithmic_bytes": mb, "note": "model bytes (SpMV + 4 basis passes per step) / batch time"},
+        "cpu_baseline": None,
+        "e2e": {"value": te["f64"] / te["f32"], "unit": "x", "h2d_bytes_per_step": 2 * 2 * 8 * int(b.size),
+                "d2h_bytes_per_step": 2 * 8 * int(b.size)},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for s_ in solvers.values():
+        s_.close()
+    return 0
+
+
 # ------------------------------------------------------------------------ our arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch(args)
     import torch
     import torch.distributed as dist
 

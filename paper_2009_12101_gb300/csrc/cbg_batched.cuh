@@ -143,20 +143,45 @@ template <int FMT> struct BatchedSolver {
         const double* va = vals + s.nz_off;
         const double* bb = a.io[0] + s.vec_off;
         double ss = 0.0;
-        for (int r = r0 + threadIdx.x; r < r1; r += BT_THREADS) {
-            double t = 0.0;
-            for (int p = rp[r]; p < rp[r + 1]; p++) {
-                double xv;
-                if constexpr (CODES) xv = code_value<FMT>(x, ci[p]);
-                else xv = reinterpret_cast<const double*>(x)[ci[p]];
-                t = __fma_rn(va[p], xv, t);
+        constexpr int RW = 4;                              // rows per thread in flight
+        for (int rb = r0 + threadIdx.x; rb < r1; rb += RW * BT_THREADS) {
+            double t[RW];
+            int p0[RW], p1[RW];
+#pragma unroll
+            for (int q = 0; q < RW; q++) {
+                const int r = rb + q * BT_THREADS;
+                t[q] = 0.0;
+                p0[q] = r < r1 ? rp[r] : 0;
+                p1[q] = r < r1 ? rp[r + 1] : 0;
             }
-            if constexpr (CODES) t = __dmul_rn(t, xscale);
-            if (residual) t = __dsub_rn(bb[r], t);
-            float hi, lo;
-            split_f64(t, hi, lo);
-            sm->ws[r - r0] = make_float2(hi, lo);
-            ss = __fma_rn(t, t, ss);
+            int len = 0;
+#pragma unroll
+            for (int q = 0; q < RW; q++) len = max(len, p1[q] - p0[q]);
+            for (int i = 0; i < len; i++) {
+#pragma unroll
+                for (int q = 0; q < RW; q++) {
+                    const int p = p0[q] + i;
+                    if (p < p1[q]) {
+                        double xv;
+                        if constexpr (CODES) xv = code_value<FMT>(x, ci[p]);
+                        else xv = reinterpret_cast<const double*>(x)[ci[p]];
+                        t[q] = __fma_rn(va[p], xv, t[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RW; q++) {
+                const int r = rb + q * BT_THREADS;
+                if (r < r1) {
+                    double v = t[q];
+                    if constexpr (CODES) v = __dmul_rn(v, xscale);
+                    if (residual) v = __dsub_rn(bb[r], v);
+                    float hi, lo;
+                    split_f64(v, hi, lo);
+                    sm->ws[r - r0] = make_float2(hi, lo);
+                    ss = __fma_rn(v, v, ss);
+                }
+            }
         }
         return ss;
     }
@@ -168,20 +193,31 @@ template <int FMT> struct BatchedSolver {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const unsigned char* Vs = a.V + s.v_off;
         const int nloc = r1 - r0;
+        constexpr int U = 8;                               // 16-byte loads in flight per lane
         for (int k = warp; k < ncols; k += BT_THREADS / 32) {
             const unsigned char* cp = Vs + ((long long)k * s.ld + r0) * BS;
             float S = 0.f, C = 0.f;
-            for (int e0 = lane * E; e0 < nloc; e0 += 32 * E) {
-                uint4 raw = ldg_stream(cp + (long long)e0 * BS);
-                Chunk<FMT> ch;
-                decode_chunk<FMT>(raw, ch);
+            for (int b0 = lane * E; b0 < nloc; b0 += U * 32 * E) {
+                uint4 raw[U];
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    const float2 wv = sm->ws[e0 + e];      // zero beyond nloc
-                    if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
-                    else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
+                for (int q = 0; q < U; q++) {
+                    const int e0 = b0 + q * 32 * E;
+                    raw[q] = e0 < nloc ? ldg_stream(cp + (long long)e0 * BS) : make_uint4(0u, 0u, 0u, 0u);
                 }
-                df_renorm(S, C);
+#pragma unroll
+                for (int q = 0; q < U; q++) {
+                    const int e0 = b0 + q * 32 * E;
+                    if (e0 >= nloc) break;
+                    Chunk<FMT> ch;
+                    decode_chunk<FMT>(raw[q], ch);
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const float2 wv = sm->ws[e0 + e];      // zero beyond nloc
+                        if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
+                        else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
+                    }
+                    df_renorm(S, C);
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -215,19 +251,28 @@ template <int FMT> struct BatchedSolver {
 #pragma unroll
             for (int e = 0; e < E; e++) { S[e] = sm->ws[e0 + e].x; C[e] = sm->ws[e0 + e].y; }
             const unsigned char* base = Vs + ((long long)r0 + e0) * BS;
-            for (int k = 0; k < ncols; k++) {
-                uint4 raw = ldg_stream(base + (long long)k * s.ld * BS);
-                Chunk<FMT> ch;
-                decode_chunk<FMT>(raw, ch);
-                const float2 c = cdf[k];
+            constexpr int U = E <= 8 ? 8 : 4;                // columns in flight per thread
+            for (int k0 = 0; k0 < ncols; k0 += U) {
+                uint4 raw[U];
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
-                    else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
-                }
-                if ((k & 3) == 3) {
+                for (int q = 0; q < U; q++)
+                    raw[q] = k0 + q < ncols ? ldg_stream(base + (long long)(k0 + q) * s.ld * BS)
+                                            : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                    for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+                for (int q = 0; q < U; q++) {
+                    if (k0 + q >= ncols) break;
+                    Chunk<FMT> ch;
+                    decode_chunk<FMT>(raw[q], ch);
+                    const float2 c = cdf[k0 + q];
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
+                        else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
+                    }
+                    if ((q & 3) == 3) {
+#pragma unroll
+                        for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+                    }
                 }
             }
 #pragma unroll
@@ -237,7 +282,9 @@ template <int FMT> struct BatchedSolver {
                     sm->ws[e0 + e] = make_float2(S[e], C[e]);
                     const double d = df_to_double(S[e], C[e]);
                     ss = __fma_rn(d, d, ss);
-                    mx = fmax(mx, fabs(d));
+                    // max |d| through the bit pattern (integer compare of non-negative doubles)
+                    const long long ab = __double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFll;
+                    mx = ab > __double_as_longlong(mx) ? __longlong_as_double(ab) : mx;
                 }
             }
         }
@@ -452,7 +499,7 @@ template <int FMT> struct BatchedSolver {
 };
 
 template <int FMT>
-__global__ void __launch_bounds__(BT_THREADS, 1) k_batched(BatchArgs a)
+__global__ void __launch_bounds__(BT_THREADS, 2) k_batched(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char bt_smem_raw[];
     BtSmem* sm = reinterpret_cast<BtSmem*>(bt_smem_raw);

@@ -120,9 +120,27 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo)
     }
 }
 
+// Exact FP32 -> FP64 conversion with integer operations (the F2F instruction runs on
+// GB300's slow FP64 pipe).  Normal numbers and zeros take the integer path; subnormal,
+// infinite and NaN inputs fall back to the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e - 1u < 254u) {
+        const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+        const unsigned int lo = (u & 7u) << 29;
+        return __hiloint2double((int)hi, (int)lo);
+    }
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
+// hi + lo rounded once to FP64: both widened exactly with integer operations, then one
+// FP64 addition
 __device__ __forceinline__ double df_to_double(float hi, float lo)
 {
-    return __dadd_rn((double)hi, (double)lo);
+    return __dadd_rn(f32_to_f64_exact(hi), f32_to_f64_exact(lo));
 }
 
 // ------------------------------------------------------------------------- decoding
@@ -201,22 +219,6 @@ template <int FMT> __device__ __forceinline__ void decode_chunk(const uint4& raw
             c.vh[2 * k + 1] = dec_i16((int)w[k] >> 16);
         }
     }
-}
-
-// Exact FP32 -> FP64 conversion with integer operations (the F2F instruction runs on
-// GB300's slow FP64 pipe).  Normal numbers and zeros take the integer path; subnormal,
-// infinite and NaN inputs fall back to the hardware conversion.
-__device__ __forceinline__ double f32_to_f64_exact(float f)
-{
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFFu;
-    if (e - 1u < 254u) {
-        const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-        const unsigned int lo = (u & 7u) << 29;
-        return __hiloint2double((int)hi, (int)lo);
-    }
-    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    return (double)f;
 }
 
 // Exact FP64 value of one code (scale not applied); used by the FP64 arithmetic mode,
