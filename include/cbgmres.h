@@ -59,6 +59,8 @@ typedef enum { CBG_ARITH_DF32 = 0, CBG_ARITH_FP64 = 1 } cbg_arith;
 /* status codes */
 #define CBG_OK                 0
 #define CBG_NOT_CONVERGED      1   /* maxit Arnoldi steps done, tau not reached        */
+#define CBG_STAGNATED          2   /* stop_on_stagnation: a restart did not lower the
+                                      explicit residual                               */
 #define CBG_ERR_ARG          (-1)  /* invalid argument                                 */
 #define CBG_ERR_NONFINITE    (-2)  /* NaN/Inf in the data or produced by the iteration */
 #define CBG_ERR_OOM          (-3)  /* device allocation failed                         */
@@ -92,7 +94,8 @@ typedef struct {
     int32_t use_graph;       /* reserved, must be 0                                     */
     int32_t profile;         /* 1: time every kernel launch with CUDA events recorded on
                                 options.stream (read with cbgmres_profile)              */
-    int32_t pad0;
+    int32_t stop_on_stagnation; /* 1: stop with CBG_STAGNATED when the explicit residual
+                                   at a restart is not below the previous one (0)      */
 } cbg_options;
 
 typedef struct {
@@ -251,6 +254,44 @@ int cbgmres_tune_batched(cbg_batch* bt, const double* b, double* x, double tol, 
 /* Set the schedule explicitly (cluster size a power of two <= 16). */
 int cbgmres_batched_schedule(cbg_batch* bt, int cluster, int split_rows);
 void cbgmres_destroy_batched(cbg_batch* bt);
+
+/* Try the handles in order (e.g. learned SPAI, Jacobi, none -- all for the same A),
+ * each continuing from the current x, until one reaches ||b - A x|| <= tol ||b||: the
+ * FP64 explicit residual is the judge.  A handle whose solve ends non-converged or
+ * stagnated hands over its x; one that produces non-finite values hands over the x it
+ * started from.  maxit caps the total Arnoldi steps.  *used = index of the handle that
+ * converged (or the last one tried).  stats accumulates over the attempts. */
+int cbgmres_solve_fallback(cbg_handle* const* hs, int nh, const double* b, double* x, double tol,
+                           int64_t maxit, cbg_stats* stats, int* used);
+
+/* ---- learned sparse approximate inverse (no counterpart in the paper) ---------------
+ * A per-row MLP (inputs: the row's 7-point stencil coefficients divided by a_ii, in the
+ * order -z,-y,-x,centre,+x,+y,+z with 0 for a missing neighbour; layers 7 -> 64 -> 64 -> 7
+ * with ReLU; BF16 weights, FP32 accumulation) emits P on A's pattern,
+ * P_{i,nb(i,k)} = out_k(i) / a_ii, for use as the right preconditioner (CBG_PC_SPAI).
+ * Training minimises mean over pairs of ||P r - e||^2 / ||e||^2 on pairs (r = A e,
+ * e = x* - x_k); each pair is folded into per-row statistics on arrival.
+ * create: A must be a 3D 7-point pattern with line stride sx and plane stride sxy (host
+ * or device CSR); weights start at a deterministic initialisation equal to Jacobi.
+ * add_pair: xstar, xk device vectors of length n.  train: `steps` Adam steps (rate lr)
+ * on all pairs so far; losses before and after.  values: P (device, nnz, A's CSR order).
+ * params: get (set = 0) or set (set = 1) the FP32 master weights (host,
+ * cbg_spai_num_params() floats: W1[64x7], b1[64], W2[64x64], b2[64], W3[7x64], b3[7]). */
+typedef struct cbg_spai cbg_spai;
+int cbg_spai_create(const cbg_csr* A, int64_t sx, int64_t sxy, const cbg_options* opt, cbg_spai** out);
+int cbg_spai_add_pair(cbg_spai* s, const double* xstar, const double* xk);
+int cbg_spai_train(cbg_spai* s, int steps, double lr, double* loss_first, double* loss_last);
+int cbg_spai_loss(cbg_spai* s, double* loss);
+int cbg_spai_values(cbg_spai* s, double* pvals);
+int cbg_spai_params(cbg_spai* s, float* params, int set);
+int cbg_spai_num_params(void);
+void cbg_spai_destroy(cbg_spai* s);
+/* One forward / backward of the MLP with given FP32 parameters (host; rounded to BF16):
+ * feat (device, rows x 7 FP32) -> out (device, rows x 7); gout (device, rows x 7) ->
+ * grad (host, cbg_spai_num_params() FP64, summed over rows).  For gradient checks. */
+int cbg_mlp_forward(int64_t rows, const float* feat, const float* params, float* out, void* stream);
+int cbg_mlp_backward(int64_t rows, const float* feat, const float* params, const float* gout,
+                     double* grad, void* stream);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,10 @@ def lib():
             L.or_dot.restype = d
             L.or_gmres.argtypes = [i64, vp, vp, vp, vp, vp, C.POINTER(GmresArgs)]
             L.or_mlp_forward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.or_spai_slots.argtypes = [i64, vp, vp, i64, i64, vp]
+            L.or_spai_accumulate.argtypes = [i64, vp, vp, vp, vp, vp, d, vp, vp, vp]
+            L.or_spai_loss.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, d, vp]
+            L.or_spai_loss.restype = d
             L.or_mlp_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp,
                                           vp, vp, vp, vp, vp, vp]
             _lib = L
@@ -236,3 +240,34 @@ def mlp_backward(feat, W1, b1, W2, b2, W3, b3, gout):
     g = [np.empty_like(t) for t in ps]
     lib().or_mlp_backward(rows, _p(feat), *[_p(t) for t in ps], _p(gout), *[_p(t) for t in g])
     return g
+
+
+# ---------------------------------------------------- learned SPAI statistics and loss
+def spai_slots(A, sx: int, sxy: int):
+    rp, ci = _c(A.rowptr, np.int32), _c(A.col, np.int32)
+    slot = np.empty(ci.size, np.int8)
+    if lib().or_spai_slots(A.n, _p(rp), _p(ci), sx, sxy, _p(slot)):
+        raise ValueError("pattern is not a 3D 7-point stencil with the given strides")
+    return slot
+
+
+def spai_accumulate(A, slot, r, e, G=None, c=None, d=None):
+    """Add one (r, e) pair (weight 1/||e||^2) to the per-row statistics."""
+    n = A.n
+    G = np.zeros((n, 49)) if G is None else G
+    c = np.zeros((n, 7)) if c is None else c
+    d = np.zeros(n) if d is None else d
+    rp, ci = _c(A.rowptr, np.int32), _c(A.col, np.int32)
+    r = _c(r, np.float64); e = _c(e, np.float64)
+    lib().or_spai_accumulate(n, _p(rp), _p(ci), _p(slot), _p(r), _p(e), 1.0 / float(e @ e),
+                             _p(G), _p(c), _p(d))
+    return G, c, d
+
+
+def spai_loss(A, slot, out, diag, G, c, d, npairs, want_grad=False):
+    rp = _c(A.rowptr, np.int32)
+    out = _c(out, np.float64); diag = _c(diag, np.float64)
+    gout = np.empty_like(out) if want_grad else None
+    loss = lib().or_spai_loss(A.n, _p(rp), _p(slot), _p(out), _p(diag), _p(G), _p(c), _p(d),
+                              float(npairs), _p(gout) if want_grad else None)
+    return (loss, gout) if want_grad else loss

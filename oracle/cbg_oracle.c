@@ -581,3 +581,58 @@ void or_vec_f32_to_e4m3(int64_t n, const float* x, uint8_t* out)
 { for (int64_t i = 0; i < n; i++) out[i] = or_f32_to_e4m3(x[i]); }
 void or_vec_e4m3_to_f64(int64_t n, const uint8_t* c, double* out)
 { for (int64_t i = 0; i < n; i++) out[i] = or_e4m3_to_f64(c[i]); }
+
+/* ===================================================================================
+ * Learned SPAI statistics (quadratic loss in the per-row SPAI values).
+ * =================================================================================== */
+int or_spai_slots(int64_t n, const int32_t* rowptr, const int32_t* col, int64_t sx, int64_t sxy,
+                  int8_t* slot)
+{
+    const int64_t off[7] = {-sxy, -sx, -1, 0, 1, sx, sxy};
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            int64_t dlt = (int64_t)col[p] - i;
+            int k = -1;
+            for (int t = 0; t < 7; t++) if (off[t] == dlt) k = t;
+            if (k < 0) return OR_ERR_ARG;
+            slot[p] = (int8_t)k;
+        }
+    return OR_OK;
+}
+
+int or_spai_accumulate(int64_t n, const int32_t* rowptr, const int32_t* col, const int8_t* slot,
+                       const double* r, const double* e, double wgt, double* G, double* c, double* d)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double rv[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++) rv[slot[p]] = r[col[p]];
+        for (int k = 0; k < 7; k++) {
+            for (int l = 0; l < 7; l++) G[i * 49 + k * 7 + l] += wgt * rv[k] * rv[l];
+            c[i * 7 + k] += wgt * e[i] * rv[k];
+        }
+        d[i] += wgt * e[i] * e[i];
+    }
+    return OR_OK;
+}
+
+double or_spai_loss(int64_t n, const int32_t* rowptr, const int8_t* slot, const double* out,
+                    const double* diag, const double* G, const double* c, const double* d,
+                    double npairs, double* gout)
+{
+    double loss = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double pv[7] = {0, 0, 0, 0, 0, 0, 0};
+        int has[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++) has[slot[p]] = 1;
+        for (int k = 0; k < 7; k++) pv[k] = has[k] ? out[i * 7 + k] / diag[i] : 0.0;
+        double li = d[i];
+        for (int k = 0; k < 7; k++) {
+            double gp = 0.0;
+            for (int l = 0; l < 7; l++) gp += G[i * 49 + k * 7 + l] * pv[l];
+            li += pv[k] * gp - 2.0 * pv[k] * c[i * 7 + k];
+            if (gout) gout[i * 7 + k] = has[k] ? 2.0 * (gp - c[i * 7 + k]) / diag[i] / npairs : 0.0;
+        }
+        loss += li;
+    }
+    return loss / npairs;
+}

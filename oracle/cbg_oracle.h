@@ -126,6 +126,22 @@ int or_mlp_backward(int64_t rows, const double* feat, const double* W1, const do
                     const double* gout /* rows x 7: dL/dout */,
                     double* gW1, double* gb1, double* gW2, double* gb2, double* gW3, double* gb3);
 
+/* ---- learned SPAI: statistics of (r, e) pairs and the loss (no counterpart in the paper:
+ * parity unpinned by the paper; pinned to finite differences and direct evaluation) ----
+ * slot[p] in 0..6 is the stencil position of nonzero p (-z,-y,-x,centre,+x,+y,+z for a
+ * 3D 7-point pattern with line stride sx and plane stride sxy).  For one pair with
+ * weight wgt = 1/||e||^2:  G_i[k][l] += wgt r_{nb(i,k)} r_{nb(i,l)},  c_i[k] += wgt e_i
+ * r_{nb(i,k)},  d_i += wgt e_i^2  (G: rows x 49, c: rows x 7, d: rows). */
+int or_spai_slots(int64_t n, const int32_t* rowptr, const int32_t* col, int64_t sx, int64_t sxy,
+                  int8_t* slot);
+int or_spai_accumulate(int64_t n, const int32_t* rowptr, const int32_t* col, const int8_t* slot,
+                       const double* r, const double* e, double wgt, double* G, double* c, double* d);
+/* loss = (1/npairs) sum_i [p_i^T G_i p_i - 2 p_i^T c_i + d_i] with p_i[k] = out[i][k] / diag_i
+ * for existing slots; gout[i][k] = dloss/dout[i][k]. */
+double or_spai_loss(int64_t n, const int32_t* rowptr, const int8_t* slot, const double* out,
+                    const double* diag, const double* G, const double* c, const double* d,
+                    double npairs, double* gout);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ FORMAT_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i
 PRECONDS = {"none": 0, "jacobi": 1, "spai": 2}
 REORTH = {"always": 0, "conditional": 1, "never": 2}
 ARITH = {"df32": 0, "fp64": 1}
-STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM",
+STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "STAGNATED", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM",
           -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_UNSUPPORTED"}
 TILE_ROWS = 4096   # padded rows per basis column (multiple of every kernel tile)
 
@@ -48,7 +48,7 @@ class Options(C.Structure):
     _fields_ = [("reorth", C.c_int32), ("precond", C.c_int32), ("arith", C.c_int32),
                 ("spmv_group", C.c_int32), ("eta", C.c_double), ("breakdown_eps", C.c_double),
                 ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32),
-                ("profile", C.c_int32), ("pad0", C.c_int32)]
+                ("profile", C.c_int32), ("stop_on_stagnation", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -112,6 +112,18 @@ def lib():
             L.cbgmres_tune_batched.argtypes = [vp, vp, vp, d, i64, C.c_char_p, C.POINTER(C.c_int),
                                                C.POINTER(C.c_int)]
             L.cbgmres_batched_schedule.argtypes = [vp, i32, i32]
+            L.cbgmres_solve_fallback.argtypes = [vp, i32, vp, vp, d, i64, C.POINTER(Stats), C.POINTER(C.c_int)]
+            L.cbg_spai_create.argtypes = [C.POINTER(Csr), i64, i64, C.POINTER(Options), C.POINTER(vp)]
+            L.cbg_spai_add_pair.argtypes = [vp, vp, vp]
+            L.cbg_spai_train.argtypes = [vp, i32, d, C.POINTER(d), C.POINTER(d)]
+            L.cbg_spai_loss.argtypes = [vp, C.POINTER(d)]
+            L.cbg_spai_values.argtypes = [vp, vp]
+            L.cbg_spai_params.argtypes = [vp, vp, i32]
+            L.cbg_spai_num_params.argtypes = []
+            L.cbg_spai_destroy.argtypes = [vp]
+            L.cbg_spai_destroy.restype = None
+            L.cbg_mlp_forward.argtypes = [i64, vp, vp, vp, vp]
+            L.cbg_mlp_backward.argtypes = [i64, vp, vp, vp, vp, vp]
             L.cbgmres_destroy_batched.argtypes = [vp]
             L.cbgmres_destroy_batched.restype = None
             _lib = L
@@ -147,7 +159,8 @@ def _dev_f64(t, n=None, name="vector"):
 
 
 def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=None,
-            check_every=4, eta=None, breakdown_eps=None, profile=False) -> Options:
+            check_every=4, eta=None, breakdown_eps=None, profile=False,
+            stop_on_stagnation=False) -> Options:
     o = Options()
     lib().cbgmres_options_default(C.byref(o))
     o.precond = PRECONDS[precond]
@@ -156,6 +169,7 @@ def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=
     o.spmv_group = spmv_group
     o.check_every = check_every
     o.profile = int(bool(profile))
+    o.stop_on_stagnation = int(bool(stop_on_stagnation))
     if eta is not None:
         o.eta = eta
     if breakdown_eps is not None:
@@ -180,7 +194,8 @@ class Solver:
 
     def __init__(self, rowptr, col, val, *, restart: int = 100, fmt: str = "f64",
                  precond: str = "none", arith: str = "df32", reorth: str = "always",
-                 spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False):
+                 spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False,
+                 stop_on_stagnation: bool = False):
         torch = _torch()
         L = lib()
         self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
@@ -197,7 +212,8 @@ class Solver:
         self.n, self.nnz = int(csr.n), int(csr.nnz)
         self.ld = (self.n + TILE_ROWS - 1) // TILE_ROWS * TILE_ROWS
         opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
-                      stream=stream, check_every=check_every, profile=profile)
+                      stream=stream, check_every=check_every, profile=profile,
+                      stop_on_stagnation=stop_on_stagnation)
         h = C.c_void_p()
         _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
                "cbgmres_create")
@@ -400,3 +416,116 @@ class BatchedSolver:
 
     def schedule(self, cluster: int, split_rows: int):
         _check(lib().cbgmres_batched_schedule(self._h, cluster, split_rows), "cbgmres_batched_schedule")
+
+
+def solve_fallback(solvers, b, x, tol: float = 1e-10, maxit: int = 100000):
+    """Try the solvers in order (same matrix), each from the current x; the FP64 explicit
+    residual decides.  Returns (stats, index of the solver that finished)."""
+    arr = (C.c_void_p * len(solvers))(*[s._h.value if s is not None else None for s in solvers])
+    st = Stats()
+    used = C.c_int()
+    n = next(s for s in solvers if s is not None).n
+    rc = lib().cbgmres_solve_fallback(C.cast(arr, C.c_void_p), len(solvers), _dev_f64(b, n, "b"),
+                                      _dev_f64(x, n, "x"), tol, maxit, C.byref(st), C.byref(used))
+    _check(rc, "cbgmres_solve_fallback")
+    return _stats_dict(st), used.value
+
+
+# ------------------------------------------------------------- learned SPAI preconditioner
+MLP_NPARAM = 5127
+
+
+class LearnedSpai:
+    """Per-row MLP emitting a sparse approximate inverse on A's 7-point pattern, trained on
+    (r, e) pairs from FP64 GMRES iterates (see cbgmres.h for the definition)."""
+
+    def __init__(self, A, sx: int, sxy: int, stream=None):
+        _torch()
+        rp = np.ascontiguousarray(A.rowptr, np.int32); ci = np.ascontiguousarray(A.col, np.int32)
+        va = np.ascontiguousarray(A.val, np.float64)
+        self._keep = (rp, ci, va)
+        csr = Csr(rp.size - 1, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, 0)
+        self.n, self.nnz = int(csr.n), int(csr.nnz)
+        opt = options(stream=stream)
+        h = C.c_void_p()
+        _check(lib().cbg_spai_create(C.byref(csr), sx, sxy, C.byref(opt), C.byref(h)), "cbg_spai_create")
+        self._h = h
+        self.npairs = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cbg_spai_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def add_pair(self, xstar, xk):
+        _check(lib().cbg_spai_add_pair(self._h, _dev_f64(xstar, self.n), _dev_f64(xk, self.n)), "cbg_spai_add_pair")
+        self.npairs += 1
+
+    def loss(self) -> float:
+        v = C.c_double()
+        _check(lib().cbg_spai_loss(self._h, C.byref(v)), "cbg_spai_loss")
+        return v.value
+
+    def train(self, steps: int = 200, lr: float = 1e-3):
+        a, b = C.c_double(), C.c_double()
+        _check(lib().cbg_spai_train(self._h, steps, lr, C.byref(a), C.byref(b)), "cbg_spai_train")
+        return a.value, b.value
+
+    def values(self):
+        torch = _torch()
+        p = torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+        _check(lib().cbg_spai_values(self._h, C.c_void_p(p.data_ptr())), "cbg_spai_values")
+        return p
+
+    def params(self) -> np.ndarray:
+        w = np.zeros(MLP_NPARAM, np.float32)
+        _check(lib().cbg_spai_params(self._h, C.c_void_p(w.ctypes.data), 0), "cbg_spai_params")
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        _check(lib().cbg_spai_params(self._h, C.c_void_p(w.ctypes.data), 1), "cbg_spai_params")
+
+    def save(self, path: str):
+        """Checkpoint: the FP32 master weights as a flat little-endian binary file."""
+        self.params().astype("<f4").tofile(path)
+
+    def load(self, path: str):
+        self.set_params(np.fromfile(path, dtype="<f4"))
+
+
+def collect_pairs(spai: LearnedSpai, solver64: "Solver", nrhs: int, iterates: int = 3, gen=None):
+    """Fold nrhs x iterates (r, e) pairs into `spai`: for random x* ~ U[-1,1] (torch
+    generator `gen`), b = A x*, the FP64-basis GMRES iterates x_0 = 0, x_1, ..., one Arnoldi
+    step apart, give e = x* - x_k and r = A e.  Only the first iterates are used: later
+    errors are dominated by smooth modes, and a per-row fit to them yields a P that
+    amplifies the rough ones (its least-squares optimum stops GMRES from converging)."""
+    torch = _torch()
+    for _ in range(nrhs):
+        xs = (torch.rand(spai.n, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1).contiguous()
+        b = solver64.spmv(xs)
+        x = torch.zeros(spai.n, dtype=torch.float64, device="cuda")
+        spai.add_pair(xs, x)
+        for _ in range(iterates - 1):
+            solver64.solve(b, x, tol=0.0, maxit=1)
+            spai.add_pair(xs, x)
+
+
+def mlp_forward(feat, params):
+    torch = _torch()
+    out = torch.empty(feat.shape[0], 7, dtype=torch.float32, device="cuda")
+    w = np.ascontiguousarray(params, np.float32)
+    _check(lib().cbg_mlp_forward(feat.shape[0], C.c_void_p(feat.data_ptr()), C.c_void_p(w.ctypes.data),
+                                 C.c_void_p(out.data_ptr()), _stream_ptr(None)), "cbg_mlp_forward")
+    return out
+
+
+def mlp_backward(feat, params, gout) -> np.ndarray:
+    w = np.ascontiguousarray(params, np.float32)
+    g = np.zeros(MLP_NPARAM)
+    _check(lib().cbg_mlp_backward(feat.shape[0], C.c_void_p(feat.data_ptr()), C.c_void_p(w.ctypes.data),
+                                  C.c_void_p(gout.data_ptr()), C.c_void_p(g.ctypes.data), _stream_ptr(None)),
+           "cbg_mlp_backward")
+    return g

@@ -588,6 +588,8 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
         const double spmv_bytes = (double)h->nnz * 12.0 + (double)(h->n + 1) * 4.0 + 16.0 * (double)h->n;
         const int L = (int)h->step_ev.size();
         long long iters_before = -1;
+        double prev_beta = INFINITY;
+        bool stagnated = false;
         for (;;) {
             enqueue_residual(h, b, x);
             launch(h, 4, 0.0, [&] { k_cycle_start<<<1, 1, 0, s>>>(h->d, maxit_eff, h->m); });
@@ -599,6 +601,11 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
             if (!hs.active) break;
             if (k_only > 0 && cycles >= 1) break;
             if (cycles > 0 && hs.iters == iters_before) return CBG_ERR_CUDA;   // no progress: device work failed
+            if (h->opt.stop_on_stagnation && cycles > 0 && !(hs.beta < prev_beta)) {
+                stagnated = true;
+                break;
+            }
+            prev_beta = hs.beta;
             iters_before = hs.iters;
             cycles++;
             enqueue_first_vector(h);
@@ -617,7 +624,7 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
         }
         if (!std::isfinite(hs.beta)) status = CBG_ERR_NONFINITE;
         else if (hs.beta <= hs.target) status = CBG_OK;
-        else status = CBG_NOT_CONVERGED;
+        else status = stagnated ? CBG_STAGNATED : CBG_NOT_CONVERGED;
     }
     CBG_CUDA(cudaEventRecord(h->ev1, s));
     CBG_CUDA(cudaEventSynchronize(h->ev1));
@@ -665,6 +672,7 @@ void cbgmres_options_default(cbg_options* o)
     o->check_every = 4;
     o->use_graph = 0;
     o->profile = 0;
+    o->stop_on_stagnation = 0;
 }
 
 const char* cbgmres_status_string(int s)
@@ -672,6 +680,7 @@ const char* cbgmres_status_string(int s)
     switch (s) {
     case CBG_OK: return "converged";
     case CBG_NOT_CONVERGED: return "not converged within maxit";
+    case CBG_STAGNATED: return "stagnated (explicit residual did not decrease over a restart)";
     case CBG_ERR_ARG: return "invalid argument";
     case CBG_ERR_NONFINITE: return "non-finite value";
     case CBG_ERR_OOM: return "device out of memory";
@@ -944,6 +953,63 @@ int cbgmres_spmv(cbg_handle* h, const double* x, double* y)
     CBG_CUDA(cudaGetLastError());
     CBG_CUDA(cudaStreamSynchronize(h->stream));
     return CBG_OK;
+}
+
+int cbgmres_solve_fallback(cbg_handle* const* hs, int nh, const double* b, double* x, double tol, int64_t maxit,
+                           cbg_stats* stats, int* used)
+{
+    if (!hs || nh < 1 || !b || !x || maxit < 0) return CBG_ERR_ARG;
+    long long n = -1;
+    for (int i = 0; i < nh; i++) {
+        if (!hs[i]) continue;
+        if (n >= 0 && hs[i]->n != n) return CBG_ERR_ARG;
+        n = hs[i]->n;
+    }
+    if (n < 0) return CBG_ERR_ARG;
+    cbg_handle* h0 = nullptr;
+    for (int i = 0; i < nh && !h0; i++) h0 = hs[i];
+    double* x0 = nullptr;
+    int rc = dalloc(&x0, n);
+    if (rc) return rc;
+    cbg_stats tot{};
+    int status = CBG_NOT_CONVERGED, last = -1;
+    long long left = maxit;
+    for (int i = 0; i < nh && left >= 0; i++) {
+        if (!hs[i]) continue;
+        last = i;
+        if (cudaMemcpyAsync(x0, x, n * sizeof(double), cudaMemcpyDeviceToDevice, h0->stream) != cudaSuccess) {
+            cudaFree(x0);
+            return CBG_ERR_CUDA;
+        }
+        cudaStreamSynchronize(h0->stream);
+        cbg_stats st{};
+        status = run_solve(hs[i], b, x, tol, left, &st, 0);
+        tot.iters += st.iters;
+        tot.restarts += st.restarts;
+        tot.reorths += st.reorths;
+        tot.ms_total += st.ms_total;
+        tot.bytes_model += st.bytes_model;
+        tot.kernel_launches += st.kernel_launches;
+        tot.true_relres = st.true_relres;
+        tot.est_relres = st.est_relres;
+        left -= st.iters;
+        if (status == CBG_OK) break;
+        if (status == CBG_ERR_NONFINITE)   // restore the iterate this attempt started from
+            cudaMemcpy(x, x0, n * sizeof(double), cudaMemcpyDeviceToDevice);
+        else if (status < 0) break;
+    }
+    cudaFree(x0);
+    if (used) *used = last;
+    if (stats) {
+        const double* hist = stats->history;
+        long long cap = stats->history_cap;
+        *stats = tot;
+        stats->history = const_cast<double*>(hist);
+        stats->history_cap = cap;
+        stats->history_len = 0;
+        stats->status = status;
+    }
+    return status;
 }
 
 void cbgmres_destroy(cbg_handle* h)
