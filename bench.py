@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
-    p.add_argument("--workload", choices=["convdiff128", "batch512"], default="convdiff128")
+    p.add_argument("--workload", choices=["convdiff128", "batch512", "random27", "learned96", "restart_sweep"],
+                   default="convdiff128")
     return p.parse_args()
 
 
@@ -301,6 +302,161 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------------ precision pattern
+R27_WORKLOAD = "random27_n1048576_band9+18_tol1e-10"
+
+
+def timed_solve(solver, b, x, tol, maxit, stream):
+    import torch
+    x.zero_()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = solver.solve(b, x, tol=tol, maxit=maxit)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), st
+
+
+def run_random27(args):
+    """bf16 / e4m3 basis with per-vector power-of-two scale vs f64 basis on the random
+    nonsymmetric n = 2^20 matrices; timed: delta 0.1, m 100; sweep: delta x m, once."""
+    import torch
+    import paper_2009_12101_gb300 as cb
+    import workloads as W
+    cb.ensure_built()
+    stream = torch.cuda.current_stream()
+    fmts = ["f64", "f32", "bf16", "e4m3"]
+    tol = 1e-10
+    results, sweep = {}, []
+    for delta in (0.01, 0.1, 0.5):
+        A = W.random27(1 << 20, delta)
+        xs = W.exact_solution(A.n, 3)
+        b = torch.from_numpy(W.rhs_from_solution(A, xs)).cuda()
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        for m in (50, 100, 200):
+            for f in fmts:
+                with cb.Solver.from_csr(A, restart=m, fmt=f, profile=True) as s:
+                    reps = args.steps if (delta == 0.1 and m == 100) else 1
+                    warm = args.warmup if (delta == 0.1 and m == 100) else 0
+                    for _ in range(warm):
+                        timed_solve(s, b, x, tol, args.maxit, stream)
+                    s.profile(reset=True)
+                    ts = []
+                    for _ in range(reps):
+                        t, st = timed_solve(s, b, x, tol, args.maxit, stream)
+                        ts.append(t)
+                    prof = s.profile()
+                    res = float(np.linalg.norm(W.rhs_from_solution(A, x.cpu().numpy()) - b.cpu().numpy())
+                                / np.linalg.norm(b.cpu().numpy()))
+                    err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+                    row = {"delta": delta, "m": m, "fmt": f, "ms": sum(ts) / len(ts), "iters": st["iters"],
+                           "status": st["status"], "true_relres": res, "x_err_vs_exact": err,
+                           "dot_gbs": (prof["basis_dot"]["bytes"] / prof["basis_dot"]["ms"] / 1e6
+                                       if prof["basis_dot"]["ms"] else None)}
+                    sweep.append(row)
+                    if delta == 0.1 and m == 100:
+                        results[f] = row
+    t = {f: results[f]["ms"] for f in fmts}
+    peak, kind = measured_peaks()
+    line = {"metric": METRIC, "value": round(t["f64"] / t["bf16"], 4), "unit": "x", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+            "config": {"workload": R27_WORKLOAD, "timed": "delta 0.1, m 100", "headline_format": "bf16",
+                       "formats": fmts, "l2": "no flush: basis >= 0.2 GB exceeds L2"},
+            "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},
+            "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_basis_dot (bf16, df32)",
+                         "achieved": round(results["bf16"]["dot_gbs"] or 0, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round((results["bf16"]["dot_gbs"] or 0) / peak, 4), "traffic": None,
+                         "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)"},
+            "sweep": sweep, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ learned preconditioner
+L96_WORKLOAD = "diffusion3d_cc96_lognormal1_learnedSPAI_f32_restart100_tol1e-10"
+
+
+def run_learned96(args):
+    """Per-row MLP SPAI trained on 2000 (r, e) pairs from FP64 GMRES, vs Jacobi and none."""
+    import torch
+    import paper_2009_12101_gb300 as cb
+    import workloads as W
+    cb.ensure_built()
+    stream = torch.cuda.current_stream()
+    N = 96
+    A = W.diffusion3d_cc(N)[0]
+    xs = W.exact_solution(A.n, 5)
+    b = torch.from_numpy(W.rhs_from_solution(A, xs)).cuda()
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda"); gen.manual_seed(20201206)
+    spai = cb.LearnedSpai(A, N, N * N)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with cb.Solver.from_csr(A, restart=10, fmt="f64", arith="fp64") as s64:
+        cb.collect_pairs(spai, s64, nrhs=667, iterates=3, gen=gen)
+    e1.record(stream); torch.cuda.synchronize()
+    t_pairs = e0.elapsed_time(e1)
+    e0.record(stream)
+    l0, l1 = spai.train(steps=400, lr=3e-3)
+    e1.record(stream); torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1)
+    pv = spai.values()
+    out = {}
+    for pc in ("none", "jacobi", "spai"):
+        with cb.Solver.from_csr(A, restart=100, fmt="f32", precond=pc) as s:
+            if pc == "spai":
+                s.set_spai(pv)
+            for _ in range(args.warmup):
+                timed_solve(s, b, x, 1e-10, args.maxit, stream)
+            ts = []
+            for _ in range(args.steps):
+                t, st = timed_solve(s, b, x, 1e-10, args.maxit, stream)
+                ts.append(t)
+            res = float(np.linalg.norm(W.rhs_from_solution(A, x.cpu().numpy()) - b.cpu().numpy())
+                        / np.linalg.norm(b.cpu().numpy()))
+            out[pc] = {"ms": sum(ts) / len(ts), "iters": st["iters"], "status": st["status"], "true_relres": res}
+    line = {"metric": METRIC, "value": round(out["jacobi"]["ms"] / out["spai"]["ms"], 4), "unit": "x",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sum(v["ms"] for v in out.values()), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+            "config": {"workload": L96_WORKLOAD, "value_is": "time(Jacobi) / time(learned SPAI), f32 basis",
+                       "pairs": spai.npairs, "train_steps": 400},
+            "solves": out, "train": {"pairs_ms": t_pairs, "train_ms": t_train, "loss_first": l0, "loss_last": l1},
+            "speedup_learned_vs_none": round(out["none"]["ms"] / out["spai"]["ms"], 4),
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+    spai.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ restart sweep (E6)
+def run_restart_sweep(args):
+    """10 fixed restart cycles for m = 10..250, every format, numerics ignored: the speedup
+    over the f64 basis as the basis share of the traffic grows (Section 5.4, Fig. restart)."""
+    import torch
+    import paper_2009_12101_gb300 as cb
+    cb.ensure_built()
+    A, xs, bnp = build_problem(args.grid)
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(bnp).cuda()
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    fmts = ["f64", "f32", "f16", "bf16", "e4m3", "i32", "i16"]
+    rows = []
+    for m in (10, 25, 50, 100, 150, 200, 250):
+        t = {}
+        for f in fmts:
+            with cb.Solver.from_csr(A, restart=m, fmt=f) as s:
+                timed_solve(s, b, x, 0.0, 10 * m, stream)
+                tt, st = timed_solve(s, b, x, 0.0, 10 * m, stream)
+                t[f] = tt
+        rows.append({"m": m, "ms": t, "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()}})
+    print(json.dumps({"metric": METRIC, "workload": f"restart_sweep_{WORKLOAD}", "cycles": 10, "rows": rows}),
+          flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -308,6 +464,12 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "random27":
+        return run_random27(args)
+    if args.workload == "learned96":
+        return run_learned96(args)
+    if args.workload == "restart_sweep":
+        return run_restart_sweep(args)
     import torch
     import torch.distributed as dist
 
