@@ -103,23 +103,17 @@ __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& 
     }
 }
 
-// Rows of w held in shared memory per chunk of the dot kernel, and the padded index
-// of row r: four row subgroups of a warp read E consecutive rows each (E * 8 bytes
-// apart); for E >= 8 their 16-byte reads would share banks, so 16 bytes of padding
-// follow every E rows (a lane's E rows stay contiguous).
-constexpr int DOT_ROWS = 4096;
-template <int E> __device__ __forceinline__ int ws_idx(int r) { return E >= 8 ? r + 2 * (r / E) : r; }
-template <int E> struct WsLen { static constexpr int value = E >= 8 ? DOT_ROWS + DOT_ROWS / 4 : DOT_ROWS; };
-
-
 // ============================================================== h = V^T w  (steps 5, 8)
-// Lane-per-column schedule: lane l of a warp owns column 8*cg + (l & 7) and row
-// subgroup l >> 3; its 16-byte loads walk down that column (eight in flight), w comes
-// from shared memory as a broadcast, and the column's partial sum stays in the lane's
-// registers until the block ends.  Each block owns one contiguous row range (persistent
-// grid of about two blocks per SM) and stages w for it in chunks of DOT_ROWS rows, so
-// there is one barrier per chunk and none in the streaming loop.  Blocks leave per-column
-// partials; the last block to finish adds them in a fixed order (deterministic).
+// Row-per-lane schedule (the axpy's): a lane owns E consecutive rows (one 16-byte code
+// chunk per column) at a time, and the 32 lanes of a warp read 512 contiguous bytes of
+// each column.  Every warp runs through its segments once per group of CG columns, keeping one
+// double-float accumulator per column (w for its rows is loaded once and reused by the CG
+// columns).  The warp then folds the CG accumulators with a transposing butterfly (each
+// level halves the columns a lane holds, so CG-1+log2(32/CG) double-float additions per
+// lane instead of 5*CG) and parks the column sums in shared memory: warps never wait for
+// one another before the end, so their load and compute phases interleave.  The block
+// sums its warps in a fixed order, blocks leave per-column partials, and the last block
+// to finish adds them in a fixed order (deterministic).
 struct DotArgs {
     const unsigned char* V;
     long long ldb;            // bytes per column
@@ -132,159 +126,187 @@ struct DotArgs {
     unsigned int* counter;
     double* out;              // [ncols]
     const int* active;        // skip when *active == 0 (may be null)
+    const float2* wdf;        // w already split into FP32 pairs (DF32 mode; may be null)
 };
 
-// Work items of the dot kernel: column group cg (8 columns) x row phase ph (the ph-th
-// of nph contiguous segments of the chunk's steps).  nph in {1, 2, 4, 8} is the smallest that spreads the items
-// evenly over the 8 warps (at most 64 items, so their accumulators fit in shared memory).
-__device__ __forceinline__ int dot_phases(int ncg)
+template <int FMT> struct DotCfg {
+    static constexpr int E = 16 / FmtInfo<FMT>::bytes;     // rows per 16-byte chunk
+    static constexpr int CG = E >= 16 ? 8 : 16;            // columns per group
+};
+
+// One level of the transposing butterfly over N double-float values per lane: lanes with
+// bit `o` set keep the upper half, the others the lower half, and each adds its
+// partner's copy of the half it keeps.
+template <int N>
+__device__ __forceinline__ void df_fold_level(float* S, float* C, int lane, int o)
 {
-    int best = 1, best_load = 1 << 30;
-    for (int nph = 1; nph <= 8; nph *= 2) {
-        const int items = ncg * nph;
-        if (items > 64) break;
-        const int load = ((items + 7) / 8) * 64 / nph;          // busiest warp, in 1/64 chunk units
-        if (load < best_load) { best_load = load; best = nph; }
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+        const float ks = up ? S[i + N / 2] : S[i], kc = up ? C[i + N / 2] : C[i];
+        const float ss = up ? S[i] : S[i + N / 2], sc = up ? C[i] : C[i + N / 2];
+        const float rs = __shfl_xor_sync(0xffffffffu, ss, o), rc = __shfl_xor_sync(0xffffffffu, sc, o);
+        float a = ks, b = kc;
+        df_add(a, b, rs, rc);
+        S[i] = a;
+        C[i] = b;
     }
-    return best;
+}
+template <int N>
+__device__ __forceinline__ void d_fold_level(double* D, int lane, int o)
+{
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+        const double k = up ? D[i + N / 2] : D[i];
+        const double snd = up ? D[i] : D[i + N / 2];
+        D[i] = __dadd_rn(k, __shfl_xor_sync(0xffffffffu, snd, o));
+    }
 }
 
-constexpr int DOT_MAXITEMS = 64;
-// dynamic shared memory of k_basis_dot: staged w, then per-(item, lane) accumulators
-template <int FMT> constexpr int dot_smem_bytes()
+// Fold CG per-lane sums into per-column warp sums.  Returns the column (0..CG-1) whose
+// total this lane holds; lanes whose bits below the transposing levels are zero hold
+// distinct columns (the others hold copies).
+template <int CG>
+__device__ __forceinline__ int df_warp_fold(float* S, float* C, int lane)
 {
-    return (WsLen<16 / FmtInfo<FMT>::bytes>::value + DOT_MAXITEMS * 32) * (int)sizeof(float2);
+    // levels o = 16, 8, ... transpose (CG = 16: four levels, CG = 8: three)
+    df_fold_level<CG>(S, C, lane, 16);
+    df_fold_level<CG / 2>(S, C, lane, 8);
+    df_fold_level<CG / 4>(S, C, lane, 4);
+    if constexpr (CG == 16) df_fold_level<2>(S, C, lane, 2);
+    int col = ((lane >> 4) & 1) * (CG / 2) + ((lane >> 3) & 1) * (CG / 4) + ((lane >> 2) & 1) * (CG / 8);
+    if constexpr (CG == 16) col += (lane >> 1) & 1;
+    // remaining levels are plain butterflies over the one value left
+#pragma unroll
+    for (int o = (CG == 16 ? 1 : 2); o >= 1; o >>= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, S[0], o), rc = __shfl_xor_sync(0xffffffffu, C[0], o);
+        df_add(S[0], C[0], rs, rc);
+    }
+    return col;
+}
+template <int CG>
+__device__ __forceinline__ int d_warp_fold(double* D, int lane)
+{
+    d_fold_level<CG>(D, lane, 16);
+    d_fold_level<CG / 2>(D, lane, 8);
+    d_fold_level<CG / 4>(D, lane, 4);
+    if constexpr (CG == 16) d_fold_level<2>(D, lane, 2);
+    int col = ((lane >> 4) & 1) * (CG / 2) + ((lane >> 3) & 1) * (CG / 4) + ((lane >> 2) & 1) * (CG / 8);
+    if constexpr (CG == 16) col += (lane >> 1) & 1;
+#pragma unroll
+    for (int o = (CG == 16 ? 1 : 2); o >= 1; o >>= 1) D[0] = __dadd_rn(D[0], __shfl_xor_sync(0xffffffffu, D[0], o));
+    return col;
+}
+
+// One column group of the dot kernel over the warp's segments.  FULL: all CG columns
+// exist (no per-column tests in the streaming loop).
+template <int FMT, int ARITH, bool FULL>
+__device__ __forceinline__ double dot_group(const DotArgs& a, int c0, int nc, long long sg0, long long nseg,
+                                            long long nwt, int lane, int& col)
+{
+    constexpr int BS = FmtInfo<FMT>::bytes;
+    constexpr int E = DotCfg<FMT>::E, CG = DotCfg<FMT>::CG;
+    const unsigned char* vbase = a.V + (long long)c0 * a.ldb;
+    float S[CG], C[CG];
+    double D[CG];
+#pragma unroll
+    for (int q = 0; q < CG; q++) { S[q] = 0.f; C[q] = 0.f; D[q] = 0.0; }
+    for (long long sg = sg0; sg < nseg; sg += nwt) {
+        const long long row0 = (sg * 32 + lane) * E;
+        const unsigned char* p = vbase + row0 * BS;
+        uint4 raw[CG];
+#pragma unroll
+        for (int q = 0; q < CG; q++)
+            raw[q] = (FULL || q < nc) ? ldg_stream(p + (long long)q * a.ldb) : make_uint4(0u, 0u, 0u, 0u);
+        float wh[E], wl[E];
+        double wd[E];
+        if (ARITH == ARITH_DF32 && a.wdf) {
+#pragma unroll
+            for (int e = 0; e < E; e += 2) {
+                const float4 w4 = __ldcg(reinterpret_cast<const float4*>(a.wdf + row0 + e));
+                wh[e] = w4.x;
+                wl[e] = w4.y;
+                wh[e + 1] = w4.z;
+                wl[e + 1] = w4.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; e += 2) {
+                const double2 w2 = __ldcg(reinterpret_cast<const double2*>(a.w + row0 + e));
+                wd[e] = w2.x;
+                wd[e + 1] = w2.y;
+            }
+            if constexpr (ARITH == ARITH_DF32) {
+#pragma unroll
+                for (int e = 0; e < E; e++) split_f64(wd[e], wh[e], wl[e]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CG; q++) {
+            if (!FULL && q >= nc) break;
+            Chunk<FMT> ch;
+            decode_chunk<FMT>(raw[q], ch);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if constexpr (ARITH == ARITH_DF32) {
+                    if constexpr (SingleFloat<FMT>::value) df_mac(S[q], C[q], ch.vh[e], wh[e], wl[e]);
+                    else df_mac2(S[q], C[q], ch.vh[e], ch.vl[e], wh[e], wl[e]);
+                } else {
+                    D[q] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), wd[e], D[q]);
+                }
+            }
+            if constexpr (ARITH == ARITH_DF32) df_renorm(S[q], C[q]);
+        }
+    }
+    if constexpr (ARITH == ARITH_DF32) {
+        col = df_warp_fold<CG>(S, C, lane);
+        return df_to_double(S[0], C[0]);
+    } else {
+        col = d_warp_fold<CG>(D, lane);
+        return D[0];
+    }
 }
 
 template <int FMT, int ARITH>
-__global__ void __launch_bounds__(THREADS, 3) k_basis_dot(DotArgs a)
+__global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
 {
     if (a.active && *a.active == 0) return;
-    constexpr int BS = FmtInfo<FMT>::bytes;
-    constexpr int E = 16 / BS;
-    constexpr int U = 8;                           // loads in flight per lane
-    extern __shared__ __align__(16) float2 dot_smem[];
-    float2* ws = dot_smem;                               // staged w (padded layout)
-    float2* acc = dot_smem + WsLen<E>::value;            // per (item, lane), owned by one warp
+    constexpr int E = DotCfg<FMT>::E, CG = DotCfg<FMT>::CG;
+    constexpr int NW = THREADS / 32;
+    constexpr int LOW = CG == 16 ? 1 : 3;          // lane bits below the transposing levels
+    __shared__ double red[NW][MAXCOLS];
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ncg = (ncols + 7) >> 3;
-    const int nph = dot_phases(ncg);
-    const int nitems = ncg * nph;
-    const int sub = lane >> 3;
 
-    for (int i = threadIdx.x; i < nitems * 32; i += THREADS) acc[i] = make_float2(0.f, 0.f);
+    // warp segments of 32 chunks (32*E rows), dealt round-robin in SM-spread order:
+    // warp w of block b takes segments w*gridDim.x + b + k*(all warps), so at any time the
+    // GPU streams one contiguous window of each column, and the last, partial round is
+    // shared by the blocks of every SM.  Warps never wait for one another until the end.
+    const long long nseg = a.nrows / (32 * E);
+    const long long nwt = (long long)gridDim.x * NW;
+    const long long sg0 = (long long)warp * gridDim.x + blockIdx.x;
 
-    // contiguous row range of this block (multiples of 64 rows)
-    const long long per = ((a.nrows + gridDim.x - 1) / gridDim.x + 63) / 64 * 64;
-    const long long rb = (long long)blockIdx.x * per;
-    const long long re = rb + per < a.nrows ? rb + per : a.nrows;
-
-    for (long long c0 = rb; c0 < re; c0 += DOT_ROWS) {
-        const int rows = (int)(re - c0 < DOT_ROWS ? re - c0 : DOT_ROWS);
-        __syncthreads();
-        {   // all of this thread's w loads in flight at once, then split into shared memory
-            constexpr int PER = DOT_ROWS / THREADS;
-            double wb[PER];
-#pragma unroll
-            for (int q = 0; q < PER; q++) {
-                const int r = threadIdx.x + q * THREADS;
-                wb[q] = r < rows ? __ldcg(a.w + c0 + r) : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < PER; q++) {
-                const int r = threadIdx.x + q * THREADS;
-                if (r < rows) {
-                    float2 sv;
-                    if constexpr (ARITH == ARITH_DF32) split_f64(wb[q], sv.x, sv.y);
-                    else sv = *reinterpret_cast<float2*>(&wb[q]);
-                    ws[ws_idx<E>(r)] = sv;
-                }
-            }
-        }
-        __syncthreads();
-        const int nsteps = rows / (4 * E);
-        for (int it = warp; it < nitems; it += THREADS / 32) {
-            const int cg = it % ncg, ph = it / ncg;
-            const int col = cg * 8 + (lane & 7);
-            if (col >= ncols) continue;
-            const unsigned char* cp = a.V + (long long)col * a.ldb + c0 * BS;
-            float S = 0.f, C = 0.f;
-            double D = 0.0;
-            // phase ph streams a contiguous segment of steps, so each warp consumes whole
-            // cache lines of its columns (interleaving phases would split a line between
-            // warps running at different times and fetch it twice)
-            const int seg = (nsteps + nph - 1) / nph;
-            const int s_beg = ph * seg;
-            const int s_end = s_beg + seg < nsteps ? s_beg + seg : nsteps;
-            for (int s0 = s_beg; s0 < s_end; s0 += U) {
-                uint4 raw[U];
-#pragma unroll
-                for (int q = 0; q < U; q++) {
-                    const int st = s0 + q;
-                    raw[q] = st < s_end ? ldg_stream(cp + (long long)(st * 4 * E + sub * E) * BS)
-                                        : make_uint4(0u, 0u, 0u, 0u);
-                }
-#pragma unroll
-                for (int q = 0; q < U; q++) {
-                    const int st = s0 + q;
-                    if (st >= s_end) break;
-                    Chunk<FMT> ch;
-                    decode_chunk<FMT>(raw[q], ch);
-                    const float2* wp = ws + ws_idx<E>(st * 4 * E + sub * E);
-#pragma unroll
-                    for (int e = 0; e < E; e++) {
-                        float2 wv = wp[e];
-                        if constexpr (ARITH == ARITH_DF32) {
-                            if constexpr (SingleFloat<FMT>::value) df_mac(S, C, ch.vh[e], wv.x, wv.y);
-                            else df_mac2(S, C, ch.vh[e], ch.vl[e], wv.x, wv.y);
-                        } else {
-                            double wd = *reinterpret_cast<const double*>(&wv);
-                            D = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), wd, D);
-                        }
-                    }
-                    if constexpr (ARITH == ARITH_DF32) df_renorm(S, C);
-                }
-            }
-            float2& slot = acc[it * 32 + lane];
-            if constexpr (ARITH == ARITH_DF32) {
-                float2 v = slot;
-                df_add(v.x, v.y, S, C);
-                slot = v;
-            } else {
-                double v = *reinterpret_cast<double*>(&slot);
-                v += D;
-                slot = *reinterpret_cast<float2*>(&v);
-            }
-        }
+    for (int c0 = 0; c0 < ncols; c0 += CG) {
+        const int nc = ncols - c0 < CG ? ncols - c0 : CG;
+        int col;
+        const double wsum = nc == CG ? dot_group<FMT, ARITH, true>(a, c0, nc, sg0, nseg, nwt, lane, col)
+                                     : dot_group<FMT, ARITH, false>(a, c0, nc, sg0, nseg, nwt, lane, col);
+        // the warp's column sums wait in shared memory for the block sum
+        if ((lane & LOW) == 0 && col < nc) red[warp][c0 + col] = wsum;
     }
-
-    // ---- block reduction: per column over its phases and row subgroups, then blocks
     __syncthreads();
+    // the block's warps in a fixed order
     for (int col = threadIdx.x; col < ncols; col += THREADS) {
-        const int cg = col >> 3, c8 = col & 7;
-        double tot;
-        if constexpr (ARITH == ARITH_DF32) {
-            float S = 0.f, C = 0.f;
-            for (int ph = 0; ph < nph; ph++)
-                for (int sb = 0; sb < 4; sb++) {
-                    float2 v = acc[(ph * ncg + cg) * 32 + sb * 8 + c8];
-                    df_add(S, C, v.x, v.y);
-                }
-            tot = df_to_double(S, C);
-        } else {
-            tot = 0.0;
-            for (int ph = 0; ph < nph; ph++)
-                for (int sb = 0; sb < 4; sb++) {
-                    float2 v = acc[(ph * ncg + cg) * 32 + sb * 8 + c8];
-                    tot += *reinterpret_cast<double*>(&v);
-                }
-        }
+        double tot = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) tot += red[w][col];
         a.part[(long long)blockIdx.x * MAXCOLS + col] = tot;
     }
+
     if (last_block(a.counter)) {
         // warp-cooperative, fixed order: lane l adds blocks l, l+32, ...; then a shuffle tree
-        for (int col = warp; col < ncols; col += THREADS / 32) {
+        for (int col = warp; col < ncols; col += NW) {
             double sum = 0.0;
             for (unsigned int b = lane; b < gridDim.x; b += 32) sum += __ldcg(a.part + (long long)b * MAXCOLS + col);
             sum = warp_sum(sum);
@@ -294,9 +316,10 @@ __global__ void __launch_bounds__(THREADS, 3) k_basis_dot(DotArgs a)
 }
 
 // ====================================================== w_out = w_in + sum_k V_k c_k
-// c_k = sign * scales[k] * coef[k].  Row-per-thread schedule: each thread owns E
-// consecutive rows, reads 16 B of every column (coalesced across the warp) and keeps E
-// double-float accumulators.  Epilogue modes:
+// c_k = sign * scales[k] * coef[k].  Row-per-lane schedule: a lane owns E consecutive
+// rows at a time, reads 16 B of every column (512 contiguous bytes across the warp) and
+// keeps E double-float accumulators; warps take 32-chunk segments round-robin in
+// SM-spread order (as in the dot kernel).  Epilogue modes:
 //   EPI_SUB   w_out = w_in - V coef, plus per-block sum of squares and max |w_out|
 //   EPI_XUPD  x += dinv .* (V coef) (dinv may be null), x = w_out, w_in unused
 //   EPI_PLAIN w_out = V coef
@@ -319,10 +342,11 @@ struct AxpyArgs {
     const int* active;
     unsigned int* counter;    // EPI_SUB final pass: last block writes st->wnorm, st->wmax
     DevState* st;
+    float2* wdf_out;          // EPI_SUB: also store w_out split into FP32 pairs (may be null)
 };
 
 template <int FMT, int ARITH, int EPI>
-__global__ void __launch_bounds__(THREADS, 2) k_basis_axpy(AxpyArgs a)
+__global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 2 ? 3 : 2) k_basis_axpy(AxpyArgs a)
 {
     if (a.active && *a.active == 0) return;
     constexpr int BS = FmtInfo<FMT>::bytes;
@@ -342,10 +366,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_axpy(AxpyArgs a)
 
     double ss = 0.0;             // epilogue partials: sum of squares (FP64) and
     unsigned long long mxb = 0;  // max |w| as the bit pattern of a non-negative double
-    const long long rows_per_block = (long long)THREADS * E;
-    const long long nblk = a.nrows / rows_per_block;
-    for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
-        const long long row0 = b * rows_per_block + (long long)threadIdx.x * E;
+    // warp segments of 32 chunks (32*E rows), dealt round-robin in SM-spread order
+    const long long nseg = a.nrows / (32 * E);
+    const long long nwt = (long long)gridDim.x * (THREADS / 32);
+    for (long long sg = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; sg < nseg; sg += nwt) {
+        const long long row0 = (sg * 32 + (threadIdx.x & 31)) * E;
         const unsigned char* base = a.V + row0 * BS;
         float S[E], C[E];
         double D[E];
@@ -413,6 +438,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_axpy(AxpyArgs a)
             }
             if constexpr (EPI == EPI_SUB) {
                 a.w_out[i] = acc;
+                if (a.wdf_out) {
+                    float2 d;
+                    split_f64(acc, d.x, d.y);
+                    a.wdf_out[i] = d;
+                }
                 if (i < a.n) {
                     ss = __fma_rn(acc, acc, ss);
                     unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & 0x7FFFFFFFFFFFFFFFull;
@@ -604,6 +634,7 @@ struct SpmvArgs {
     DevState* st;             // Arnoldi: omega; residual: beta, rinf, active
     int* flag_host;
     const int* active;
+    float2* ydf;              // Arnoldi: also store y split into FP32 pairs (may be null)
 };
 
 template <int XFMT, int GROUP, int MODE>
@@ -642,6 +673,13 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
             if constexpr (MODE == SPMV_RESIDUAL) yv = __dsub_rn(a.b[row], s);
             if constexpr (MODE == SPMV_ACCUM) yv = __dadd_rn(a.y[row], s);
             a.y[row] = yv;
+            if constexpr (MODE == SPMV_ARNOLDI) {
+                if (a.ydf) {
+                    float2 d;
+                    split_f64(yv, d.x, d.y);
+                    a.ydf[row] = d;
+                }
+            }
             ss = __fma_rn(yv, yv, ss);
             mx = fmax(mx, fabs(yv));
         }

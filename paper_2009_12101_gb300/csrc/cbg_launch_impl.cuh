@@ -14,26 +14,10 @@ namespace cbg {
     default: k_spmv<XF, 32, MODE><<<grid, THREADS, 0, s>>>(a); break;                          \
     }
 
-// the dot kernel uses more than the 48 KB of default dynamic shared memory: opt in once
-// (per process; the attribute applies to every device)
-template <int FMT> static void dot_opt_in()
-{
-    static const bool done = [] {
-        cudaFuncSetAttribute(k_basis_dot<FMT, ARITH_DF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             dot_smem_bytes<FMT>());
-        cudaFuncSetAttribute(k_basis_dot<FMT, ARITH_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             dot_smem_bytes<FMT>());
-        return true;
-    }();
-    (void)done;
-}
-
 template <int FMT> void Launcher<FMT>::dot(int arith, int grid, cudaStream_t s, const DotArgs& a)
 {
-    dot_opt_in<FMT>();
-    constexpr int smem = dot_smem_bytes<FMT>();
-    if (arith == ARITH_DF32) k_basis_dot<FMT, ARITH_DF32><<<grid, THREADS, smem, s>>>(a);
-    else k_basis_dot<FMT, ARITH_FP64><<<grid, THREADS, smem, s>>>(a);
+    if (arith == ARITH_DF32) k_basis_dot<FMT, ARITH_DF32><<<grid, THREADS, 0, s>>>(a);
+    else k_basis_dot<FMT, ARITH_FP64><<<grid, THREADS, 0, s>>>(a);
 }
 
 template <int FMT>
@@ -78,9 +62,8 @@ void Launcher<FMT>::decode(int grid, cudaStream_t s, const unsigned char* codes,
 
 template <int FMT> int Launcher<FMT>::occupancy_dot()
 {
-    dot_opt_in<FMT>();
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_basis_dot<FMT, ARITH_DF32>, THREADS, dot_smem_bytes<FMT>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_basis_dot<FMT, ARITH_DF32>, THREADS, 0);
     return b;
 }
 

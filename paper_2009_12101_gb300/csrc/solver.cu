@@ -262,6 +262,7 @@ struct cbg_handle {
     // basis and vectors
     unsigned char* V = nullptr;
     double *w = nullptr, *w1 = nullptr, *w2 = nullptr, *r = nullptr, *tmp = nullptr, *z = nullptr;
+    double* wdf = nullptr;    // w (then w1) split into FP32 pairs for the DF32 dot kernel (float2[ld])
     double *bdev = nullptr, *xdev = nullptr;   // staging for cbgmres_solve_host
     double* scratch = nullptr;                 // small reductions
     // solver state
@@ -288,7 +289,7 @@ void free_handle(cbg_handle* h)
 {
     if (!h) return;
     cudaFree(h->rowptr); cudaFree(h->col); cudaFree(h->val); cudaFree(h->valp); cudaFree(h->dinv);
-    cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
+    cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->wdf); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
     cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
     cudaFree(h->state_block); cudaFree(h->d.hist);
     if (h->flag_host) cudaFreeHost(h->flag_host);
@@ -401,6 +402,7 @@ void enqueue_step(cbg_handle* h, int j)
     cudaStream_t s = h->stream;
     const int* active = &h->d.st->active;
     const unsigned char* Vj = h->V + (long long)j * h->ldb;
+    float2* wdf = h->opt.arith == CBG_ARITH_DF32 ? reinterpret_cast<float2*>(h->wdf) : nullptr;
     // steps 3-4: w = A M^{-1} v_j, omega
     {
         SpmvArgs a = spmv_args(h);
@@ -417,11 +419,13 @@ void enqueue_step(cbg_handle* h, int j)
             b2.x = h->z;
             b2.xscale = 1.0;
             b2.y = h->w;
+            b2.ydf = wdf;
             b2.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
         } else {
             a.val = h->valp ? h->valp : h->val;
             a.y = h->w;
+            a.ydf = wdf;
             a.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
         }
@@ -439,6 +443,7 @@ void enqueue_step(cbg_handle* h, int j)
     da.part = h->d.part;
     da.active = active;
     da.w = h->w;
+    da.wdf = wdf;
     da.counter = h->d.counters + 2;
     da.out = h->d.h;
     launch(h, 0, pass_bytes, [&] { op.dot(h->opt.arith, h->grid_dot, s, da); });
@@ -458,6 +463,7 @@ void enqueue_step(cbg_handle* h, int j)
     xa.w_out = reorth ? h->w1 : h->w2;
     xa.st = h->d.st;
     xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
+    xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
     launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     if (reorth) {
         // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
@@ -468,6 +474,7 @@ void enqueue_step(cbg_handle* h, int j)
         xa.coef = h->d.u;
         xa.w_in = h->w1;
         xa.w_out = h->w2;
+        xa.wdf_out = nullptr;
         xa.counter = h->d.counters + 5;
         launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
     }
@@ -772,7 +779,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     }
     TRY(dalloc(&h->V, (size_t)(restart + 1) * h->ldb));
     if (cudaMemset(h->V, 0, (size_t)(restart + 1) * h->ldb) != cudaSuccess) TRY(CBG_ERR_CUDA);
-    double** vecs[] = {&h->w, &h->w1, &h->w2, &h->r, &h->tmp, &h->z};
+    double** vecs[] = {&h->w, &h->w1, &h->w2, &h->r, &h->tmp, &h->z, &h->wdf};
     for (double** p : vecs) {
         TRY(dalloc(p, h->ld));
         if (cudaMemset(*p, 0, h->ld * sizeof(double)) != cudaSuccess) TRY(CBG_ERR_CUDA);
