@@ -79,6 +79,57 @@ __device__ __forceinline__ void df_renorm(float& S, float& C)
     C = e;
 }
 
+// ---- the same operations on two independent accumulations at once, on the packed
+// FP32x2 pipe of sm_100-class GPUs (one instruction per pair).  Subtractions are written
+// as FMAs with a -1 multiplier, which round exactly like the subtraction, so every
+// component is bitwise identical to the scalar routine above.
+__device__ __forceinline__ float2 f2_neg1() { return make_float2(-1.f, -1.f); }
+
+// (S + C) += v * (wh + wl) per component; nwh = -wh, v exact FP32
+__device__ __forceinline__ void df2_mac(float2& S, float2& C, float2 v, float2 wh, float2 nwh, float2 wl)
+{
+    const float2 m1 = f2_neg1();
+    const float2 np = __fmul2_rn(v, nwh);           // -p, p = RN(v*wh)
+    float2 pe = __ffma2_rn(v, wh, np);              // v*wh - p, exact
+    pe = __ffma2_rn(v, wl, pe);
+    const float2 s = __ffma2_rn(np, m1, S);         // TwoSum(S, p): s = S + p
+    const float2 bb = __ffma2_rn(S, m1, s);         // s - S
+    const float2 t1 = __ffma2_rn(bb, m1, s);        // s - bb
+    const float2 t2 = __ffma2_rn(t1, m1, S);        // S - (s - bb)
+    const float2 u = __fadd2_rn(np, bb);            // -(p - bb)
+    const float2 e = __ffma2_rn(u, m1, t2);         // t2 + (p - bb)
+    C = __fadd2_rn(C, __fadd2_rn(e, pe));
+    S = s;
+}
+
+// (S + C) += (vh + vl) * (wh + wl) per component, for codes that need an FP32 pair
+__device__ __forceinline__ void df2_mac2(float2& S, float2& C, float2 vh, float2 vl, float2 wh, float2 nwh,
+                                         float2 wl)
+{
+    const float2 m1 = f2_neg1();
+    const float2 np = __fmul2_rn(vh, nwh);
+    float2 pe = __ffma2_rn(vh, wh, np);
+    pe = __ffma2_rn(vh, wl, pe);
+    pe = __ffma2_rn(vl, wh, pe);
+    const float2 s = __ffma2_rn(np, m1, S);
+    const float2 bb = __ffma2_rn(S, m1, s);
+    const float2 t1 = __ffma2_rn(bb, m1, s);
+    const float2 t2 = __ffma2_rn(t1, m1, S);
+    const float2 u = __fadd2_rn(np, bb);
+    const float2 e = __ffma2_rn(u, m1, t2);
+    C = __fadd2_rn(C, __fadd2_rn(e, pe));
+    S = s;
+}
+
+__device__ __forceinline__ void df2_renorm(float2& S, float2& C)
+{
+    const float2 m1 = f2_neg1();
+    const float2 s = __fadd2_rn(S, C);
+    const float2 d = __ffma2_rn(S, m1, s);          // s - S
+    C = __ffma2_rn(d, m1, C);                       // C - (s - S)
+    S = s;
+}
+
 // (aS + aC) += (bS + bC)
 __device__ __forceinline__ void df_add(float& aS, float& aC, float bS, float bC)
 {

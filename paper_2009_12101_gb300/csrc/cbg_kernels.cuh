@@ -37,7 +37,7 @@ struct DevState {
     double hn;            // h_{j+1,j}
     long long hist_cap;
     int last_k;           // columns of the previous cycle (set when a cycle starts)
-    int pad0;
+    int fault;            // nonzero: a pipelined kernel gave up waiting (FAULT_TIMEOUT)
     double wnorm, wmax;   // ||w||_2 and ||w||_inf of the orthogonalised w (last axpy block)
 };
 
@@ -126,7 +126,7 @@ struct DotArgs {
     unsigned int* counter;
     double* out;              // [ncols]
     const int* active;        // skip when *active == 0 (may be null)
-    const float2* wdf;        // w already split into FP32 pairs (DF32 mode; may be null)
+    const float* wdf;         // w split into FP32 pairs, planar: hi[nrows] then lo[nrows] (DF32; may be null)
 };
 
 template <int FMT> struct DotCfg {
@@ -164,22 +164,31 @@ __device__ __forceinline__ void d_fold_level(double* D, int lane, int o)
     }
 }
 
-// Fold CG per-lane sums into per-column warp sums.  Returns the column (0..CG-1) whose
-// total this lane holds; lanes whose bits below the transposing levels are zero hold
-// distinct columns (the others hold copies).
+// Fold CG per-lane sums (CG = 4, 8 or 16) into per-column warp sums.  Returns the column
+// (0..CG-1) whose total this lane holds; lanes whose bits below the transposing levels
+// (lane & fold_low<CG>()) are zero hold distinct columns (the others hold copies).
+template <int CG> __host__ __device__ constexpr int fold_low() { return CG == 16 ? 1 : (CG == 8 ? 3 : 7); }
+
 template <int CG>
 __device__ __forceinline__ int df_warp_fold(float* S, float* C, int lane)
 {
-    // levels o = 16, 8, ... transpose (CG = 16: four levels, CG = 8: three)
+    static_assert(CG == 4 || CG == 8 || CG == 16, "fold width");
+    int col = 0;
     df_fold_level<CG>(S, C, lane, 16);
+    col += ((lane >> 4) & 1) * (CG / 2);
     df_fold_level<CG / 2>(S, C, lane, 8);
-    df_fold_level<CG / 4>(S, C, lane, 4);
-    if constexpr (CG == 16) df_fold_level<2>(S, C, lane, 2);
-    int col = ((lane >> 4) & 1) * (CG / 2) + ((lane >> 3) & 1) * (CG / 4) + ((lane >> 2) & 1) * (CG / 8);
-    if constexpr (CG == 16) col += (lane >> 1) & 1;
-    // remaining levels are plain butterflies over the one value left
+    col += ((lane >> 3) & 1) * (CG / 4);
+    if constexpr (CG >= 8) {
+        df_fold_level<CG / 4>(S, C, lane, 4);
+        col += ((lane >> 2) & 1) * (CG / 8);
+    }
+    if constexpr (CG == 16) {
+        df_fold_level<2>(S, C, lane, 2);
+        col += (lane >> 1) & 1;
+    }
+    // the remaining levels are plain butterflies over the one value left
 #pragma unroll
-    for (int o = (CG == 16 ? 1 : 2); o >= 1; o >>= 1) {
+    for (int o = (fold_low<CG>() + 1) / 2; o >= 1; o >>= 1) {
         const float rs = __shfl_xor_sync(0xffffffffu, S[0], o), rc = __shfl_xor_sync(0xffffffffu, C[0], o);
         df_add(S[0], C[0], rs, rc);
     }
@@ -188,14 +197,22 @@ __device__ __forceinline__ int df_warp_fold(float* S, float* C, int lane)
 template <int CG>
 __device__ __forceinline__ int d_warp_fold(double* D, int lane)
 {
+    static_assert(CG == 4 || CG == 8 || CG == 16, "fold width");
+    int col = 0;
     d_fold_level<CG>(D, lane, 16);
+    col += ((lane >> 4) & 1) * (CG / 2);
     d_fold_level<CG / 2>(D, lane, 8);
-    d_fold_level<CG / 4>(D, lane, 4);
-    if constexpr (CG == 16) d_fold_level<2>(D, lane, 2);
-    int col = ((lane >> 4) & 1) * (CG / 2) + ((lane >> 3) & 1) * (CG / 4) + ((lane >> 2) & 1) * (CG / 8);
-    if constexpr (CG == 16) col += (lane >> 1) & 1;
+    col += ((lane >> 3) & 1) * (CG / 4);
+    if constexpr (CG >= 8) {
+        d_fold_level<CG / 4>(D, lane, 4);
+        col += ((lane >> 2) & 1) * (CG / 8);
+    }
+    if constexpr (CG == 16) {
+        d_fold_level<2>(D, lane, 2);
+        col += (lane >> 1) & 1;
+    }
 #pragma unroll
-    for (int o = (CG == 16 ? 1 : 2); o >= 1; o >>= 1) D[0] = __dadd_rn(D[0], __shfl_xor_sync(0xffffffffu, D[0], o));
+    for (int o = (fold_low<CG>() + 1) / 2; o >= 1; o >>= 1) D[0] = __dadd_rn(D[0], __shfl_xor_sync(0xffffffffu, D[0], o));
     return col;
 }
 
@@ -208,10 +225,12 @@ __device__ __forceinline__ double dot_group(const DotArgs& a, int c0, int nc, lo
     constexpr int BS = FmtInfo<FMT>::bytes;
     constexpr int E = DotCfg<FMT>::E, CG = DotCfg<FMT>::CG;
     const unsigned char* vbase = a.V + (long long)c0 * a.ldb;
-    float S[CG], C[CG];
+    float2 S2[CG / 2], C2[CG / 2];       // columns (2i, 2i+1) on the packed FP32x2 pipe
     double D[CG];
 #pragma unroll
-    for (int q = 0; q < CG; q++) { S[q] = 0.f; C[q] = 0.f; D[q] = 0.0; }
+    for (int q = 0; q < CG / 2; q++) { S2[q] = make_float2(0.f, 0.f); C2[q] = make_float2(0.f, 0.f); }
+#pragma unroll
+    for (int q = 0; q < CG; q++) D[q] = 0.0;
     for (long long sg = sg0; sg < nseg; sg += nwt) {
         const long long row0 = (sg * 32 + lane) * E;
         const unsigned char* p = vbase + row0 * BS;
@@ -222,13 +241,18 @@ __device__ __forceinline__ double dot_group(const DotArgs& a, int c0, int nc, lo
         float wh[E], wl[E];
         double wd[E];
         if (ARITH == ARITH_DF32 && a.wdf) {
+            if constexpr (E == 2) {
+                const float2 h2 = __ldcg(reinterpret_cast<const float2*>(a.wdf + row0));
+                const float2 l2 = __ldcg(reinterpret_cast<const float2*>(a.wdf + a.nrows + row0));
+                wh[0] = h2.x; wh[1] = h2.y; wl[0] = l2.x; wl[1] = l2.y;
+            } else {
 #pragma unroll
-            for (int e = 0; e < E; e += 2) {
-                const float4 w4 = __ldcg(reinterpret_cast<const float4*>(a.wdf + row0 + e));
-                wh[e] = w4.x;
-                wl[e] = w4.y;
-                wh[e + 1] = w4.z;
-                wl[e + 1] = w4.w;
+                for (int e = 0; e < E; e += 4) {
+                    const float4 h4 = __ldcg(reinterpret_cast<const float4*>(a.wdf + row0 + e));
+                    const float4 l4 = __ldcg(reinterpret_cast<const float4*>(a.wdf + a.nrows + row0 + e));
+                    wh[e] = h4.x; wh[e + 1] = h4.y; wh[e + 2] = h4.z; wh[e + 3] = h4.w;
+                    wl[e] = l4.x; wl[e + 1] = l4.y; wl[e + 2] = l4.z; wl[e + 3] = l4.w;
+                }
             }
         } else {
 #pragma unroll
@@ -242,24 +266,46 @@ __device__ __forceinline__ double dot_group(const DotArgs& a, int c0, int nc, lo
                 for (int e = 0; e < E; e++) split_f64(wd[e], wh[e], wl[e]);
             }
         }
+        if constexpr (ARITH == ARITH_DF32) {
+            // a missing column (q >= nc) has zero codes and adds exact zeros
 #pragma unroll
-        for (int q = 0; q < CG; q++) {
-            if (!FULL && q >= nc) break;
-            Chunk<FMT> ch;
-            decode_chunk<FMT>(raw[q], ch);
+            for (int q = 0; q < CG; q += 2) {
+                if (!FULL && q >= nc) break;
+                Chunk<FMT> c0h, c1h;
+                decode_chunk<FMT>(raw[q], c0h);
+                decode_chunk<FMT>(raw[q + 1], c1h);
 #pragma unroll
-            for (int e = 0; e < E; e++) {
-                if constexpr (ARITH == ARITH_DF32) {
-                    if constexpr (SingleFloat<FMT>::value) df_mac(S[q], C[q], ch.vh[e], wh[e], wl[e]);
-                    else df_mac2(S[q], C[q], ch.vh[e], ch.vl[e], wh[e], wl[e]);
-                } else {
-                    D[q] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), wd[e], D[q]);
+                for (int e = 0; e < E; e++) {
+                    const float2 wh2 = make_float2(wh[e], wh[e]), nwh2 = make_float2(-wh[e], -wh[e]);
+                    const float2 wl2 = make_float2(wl[e], wl[e]);
+                    if constexpr (SingleFloat<FMT>::value)
+                        df2_mac(S2[q / 2], C2[q / 2], make_float2(c0h.vh[e], c1h.vh[e]), wh2, nwh2, wl2);
+                    else
+                        df2_mac2(S2[q / 2], C2[q / 2], make_float2(c0h.vh[e], c1h.vh[e]),
+                                 make_float2(c0h.vl[e], c1h.vl[e]), wh2, nwh2, wl2);
                 }
+                df2_renorm(S2[q / 2], C2[q / 2]);
             }
-            if constexpr (ARITH == ARITH_DF32) df_renorm(S[q], C[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < CG; q++) {
+                if (!FULL && q >= nc) break;
+                Chunk<FMT> ch;
+                decode_chunk<FMT>(raw[q], ch);
+#pragma unroll
+                for (int e = 0; e < E; e++) D[q] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), wd[e], D[q]);
+            }
         }
     }
     if constexpr (ARITH == ARITH_DF32) {
+        float S[CG], C[CG];
+#pragma unroll
+        for (int q = 0; q < CG / 2; q++) {
+            S[2 * q] = S2[q].x;
+            S[2 * q + 1] = S2[q].y;
+            C[2 * q] = C2[q].x;
+            C[2 * q + 1] = C2[q].y;
+        }
         col = df_warp_fold<CG>(S, C, lane);
         return df_to_double(S[0], C[0]);
     } else {
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
     if (a.active && *a.active == 0) return;
     constexpr int E = DotCfg<FMT>::E, CG = DotCfg<FMT>::CG;
     constexpr int NW = THREADS / 32;
-    constexpr int LOW = CG == 16 ? 1 : 3;          // lane bits below the transposing levels
+    constexpr int LOW = fold_low<CG>();            // lane bits below the transposing levels
     __shared__ double red[NW][MAXCOLS];
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -342,7 +388,7 @@ struct AxpyArgs {
     const int* active;
     unsigned int* counter;    // EPI_SUB final pass: last block writes st->wnorm, st->wmax
     DevState* st;
-    float2* wdf_out;          // EPI_SUB: also store w_out split into FP32 pairs (may be null)
+    float* wdf_out;           // EPI_SUB: also store w_out split, planar hi[nrows] then lo[nrows] (may be null)
 };
 
 template <int FMT, int ARITH, int EPI>
@@ -372,10 +418,31 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 2 ? 3 : 2) k_b
     for (long long sg = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; sg < nseg; sg += nwt) {
         const long long row0 = (sg * 32 + (threadIdx.x & 31)) * E;
         const unsigned char* base = a.V + row0 * BS;
-        float S[E], C[E];
+        float2 S2[E / 2], C2[E / 2];     // rows (2i, 2i+1) on the packed FP32x2 pipe
         double D[E];
 #pragma unroll
-        for (int e = 0; e < E; e++) { S[e] = 0.f; C[e] = 0.f; D[e] = 0.0; }
+        for (int e = 0; e < E / 2; e++) { S2[e] = make_float2(0.f, 0.f); C2[e] = make_float2(0.f, 0.f); }
+#pragma unroll
+        for (int e = 0; e < E; e++) D[e] = 0.0;
+        auto column = [&](const uint4& raw, float2 c) {
+            Chunk<FMT> ch;
+            decode_chunk<FMT>(raw, ch);
+            if constexpr (ARITH == ARITH_DF32) {
+                const float2 ch2 = make_float2(c.x, c.x), nch2 = make_float2(-c.x, -c.x), cl2 = make_float2(c.y, c.y);
+#pragma unroll
+                for (int e = 0; e < E; e += 2) {
+                    if constexpr (SingleFloat<FMT>::value)
+                        df2_mac(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]), ch2, nch2, cl2);
+                    else
+                        df2_mac2(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]),
+                                 make_float2(ch.vl[e], ch.vl[e + 1]), ch2, nch2, cl2);
+                }
+            } else {
+                const double cd = *reinterpret_cast<double*>(&c);
+#pragma unroll
+                for (int e = 0; e < E; e++) D[e] = __fma_rn(chunk_f64<FMT>(raw, ch, e), cd, D[e]);
+            }
+        };
         int k = 0;
         for (; k + U <= ncols; k += U) {
             uint4 raw[U];
@@ -383,42 +450,23 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 2 ? 3 : 2) k_b
             for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
 #pragma unroll
             for (int q = 0; q < U; q++) {
-                Chunk<FMT> ch;
-                decode_chunk<FMT>(raw[q], ch);
-                float2 c = cs[k + q];
-#pragma unroll
-                for (int e = 0; e < E; e++) {
-                    if constexpr (ARITH == ARITH_DF32) {
-                        if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
-                        else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
-                    } else {
-                        double cd = *reinterpret_cast<double*>(&c);
-                        D[e] = __fma_rn(chunk_f64<FMT>(raw[q], ch, e), cd, D[e]);
-                    }
-                }
+                column(raw[q], cs[k + q]);
                 if constexpr (ARITH == ARITH_DF32) {
                     if ((q & 3) == 3) {
 #pragma unroll
-                        for (int e = 0; e < E; e++) df_renorm(S[e], C[e]);
+                        for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
                     }
                 }
             }
         }
-        for (; k < ncols; k++) {
-            uint4 raw = ldg_stream(base + (long long)k * a.ldb);
-            Chunk<FMT> ch;
-            decode_chunk<FMT>(raw, ch);
-            float2 c = cs[k];
+        for (; k < ncols; k++) column(ldg_stream(base + (long long)k * a.ldb), cs[k]);
+        float S[E], C[E];
 #pragma unroll
-            for (int e = 0; e < E; e++) {
-                if constexpr (ARITH == ARITH_DF32) {
-                    if constexpr (SingleFloat<FMT>::value) df_mac(S[e], C[e], ch.vh[e], c.x, c.y);
-                    else df_mac2(S[e], C[e], ch.vh[e], ch.vl[e], c.x, c.y);
-                } else {
-                    double cd = *reinterpret_cast<double*>(&c);
-                    D[e] = __fma_rn(chunk_f64<FMT>(raw, ch, e), cd, D[e]);
-                }
-            }
+        for (int e = 0; e < E / 2; e++) {
+            S[2 * e] = S2[e].x;
+            S[2 * e + 1] = S2[e].y;
+            C[2 * e] = C2[e].x;
+            C[2 * e + 1] = C2[e].y;
         }
         // epilogue
 #pragma unroll
@@ -439,9 +487,10 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 2 ? 3 : 2) k_b
             if constexpr (EPI == EPI_SUB) {
                 a.w_out[i] = acc;
                 if (a.wdf_out) {
-                    float2 d;
-                    split_f64(acc, d.x, d.y);
-                    a.wdf_out[i] = d;
+                    float h, l;
+                    split_f64(acc, h, l);
+                    a.wdf_out[i] = h;
+                    a.wdf_out[a.nrows + i] = l;
                 }
                 if (i < a.n) {
                     ss = __fma_rn(acc, acc, ss);
@@ -634,7 +683,8 @@ struct SpmvArgs {
     DevState* st;             // Arnoldi: omega; residual: beta, rinf, active
     int* flag_host;
     const int* active;
-    float2* ydf;              // Arnoldi: also store y split into FP32 pairs (may be null)
+    float* ydf;               // Arnoldi: also store y split, planar hi[ydf_ld] then lo (may be null)
+    long long ydf_ld;
 };
 
 template <int XFMT, int GROUP, int MODE>
@@ -675,9 +725,10 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
             a.y[row] = yv;
             if constexpr (MODE == SPMV_ARNOLDI) {
                 if (a.ydf) {
-                    float2 d;
-                    split_f64(yv, d.x, d.y);
-                    a.ydf[row] = d;
+                    float h, l;
+                    split_f64(yv, h, l);
+                    a.ydf[row] = h;
+                    a.ydf[a.ydf_ld + row] = l;
                 }
             }
             ss = __fma_rn(yv, yv, ss);

@@ -6,12 +6,16 @@
 
 #include "cbg_batched.cuh"
 #include "cbg_kernels.cuh"
+#include "cbg_stream.cuh"
 
 namespace cbg {
 
 template <int FMT> struct Launcher {
     static void dot(int arith, int grid, cudaStream_t s, const DotArgs& a);
     static void axpy(int arith, int epi, int grid, cudaStream_t s, const AxpyArgs& a);
+    // bulk-copy pipelined DF32 dot (one block per SM)
+    static void dot_tma(int grid, cudaStream_t s, const DotArgs& a, int* fault);
+    static bool tma_fits();
     static void store(int grid, cudaStream_t s, const StoreArgs& a);
     static void spmv_code(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a);
     static void encode(int grid, cudaStream_t s, const double* v, long long n, unsigned char* codes,

@@ -1,5 +1,7 @@
 // cbg_launch_impl.cuh -- definitions of the launchers declared in cbg_launch.h.
 #pragma once
+#include <algorithm>
+
 #include "cbg_launch.h"
 
 namespace cbg {
@@ -32,6 +34,37 @@ void Launcher<FMT>::axpy(int arith, int epi, int grid, cudaStream_t s, const Axp
         else if (epi == EPI_XUPD) k_basis_axpy<FMT, ARITH_FP64, EPI_XUPD><<<grid, THREADS, 0, s>>>(a);
         else k_basis_axpy<FMT, ARITH_FP64, EPI_PLAIN><<<grid, THREADS, 0, s>>>(a);
     }
+}
+
+// Ring stages of the pipelined dot: the opt-in shared memory left by the kernel's static
+// shared memory (queried once per process), and the matching opt-in attribute.
+struct TmaPlan {
+    int stages = 0;
+    size_t smem = 0;
+};
+template <int FMT> static const TmaPlan& tma_plan()
+{
+    static const TmaPlan plan = [] {
+        using G = TmaGeom<FMT>;
+        TmaPlan p;
+        cudaFuncAttributes fa{};
+        const int static_bytes =
+            cudaFuncGetAttributes(&fa, k_basis_dot_tma<FMT>) == cudaSuccess ? (int)fa.sharedSizeBytes : TMA_SMEM_OPTIN;
+        p.stages = tma_stages(G::STAGE_DOT, static_bytes);
+        p.smem = tma_smem_bytes(p.stages, G::STAGE_DOT);
+        if (p.stages >= 2)
+            cudaFuncSetAttribute(k_basis_dot_tma<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        return p;
+    }();
+    return plan;
+}
+
+template <int FMT> bool Launcher<FMT>::tma_fits() { return tma_plan<FMT>().stages >= 2; }
+
+template <int FMT> void Launcher<FMT>::dot_tma(int grid, cudaStream_t s, const DotArgs& a, int* fault)
+{
+    const TmaPlan& p = tma_plan<FMT>();
+    k_basis_dot_tma<FMT><<<grid, DOT_THREADS, p.smem, s>>>(a, p.stages, fault);
 }
 
 template <int FMT> void Launcher<FMT>::store(int grid, cudaStream_t s, const StoreArgs& a)

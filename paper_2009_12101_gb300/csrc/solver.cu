@@ -69,6 +69,8 @@ int num_sms()
 struct Ops {
     void (*dot)(int, int, cudaStream_t, const DotArgs&);
     void (*axpy)(int, int, int, cudaStream_t, const AxpyArgs&);
+    void (*dot_tma)(int, cudaStream_t, const DotArgs&, int*);
+    bool (*tma_fits)();
     void (*store)(int, cudaStream_t, const StoreArgs&);
     void (*spmv_code)(int, int, int, cudaStream_t, const SpmvArgs&);
     void (*encode)(int, cudaStream_t, const double*, long long, unsigned char*, EncParams);
@@ -79,7 +81,8 @@ struct Ops {
 
 template <int F> Ops make_ops()
 {
-    return Ops{&Launcher<F>::dot, &Launcher<F>::axpy, &Launcher<F>::store, &Launcher<F>::spmv_code,
+    return Ops{&Launcher<F>::dot, &Launcher<F>::axpy, &Launcher<F>::dot_tma,
+               &Launcher<F>::tma_fits, &Launcher<F>::store, &Launcher<F>::spmv_code,
                &Launcher<F>::encode, &Launcher<F>::decode, &Launcher<F>::occupancy_dot,
                &Launcher<F>::occupancy_axpy};
 }
@@ -94,6 +97,17 @@ const Ops& ops_for(int fmt)
 long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
 
 // --------------------------------------------------------------- small helper kernels
+// w as double-float hi and lo planes, for the dot kernels
+__global__ void k_split_df(const double* w, long long n, float* out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float h, l;
+        split_f64(w[i], h, l);
+        out[i] = h;
+        out[n + i] = l;
+    }
+}
+
 __global__ void k_jacobi_prepare(const int* rowptr, const int* col, const double* val, long long n,
                                  double* dinv, int* bad)
 {
@@ -133,6 +147,7 @@ __global__ void k_init_state(DevState* st, double bnorm, double target, double e
     st->hn = 0.0;
     st->hist_cap = hist_cap;
     st->last_k = 0;
+    st->fault = 0;
 }
 
 // ================================================ cycle start / end (single block)
@@ -262,7 +277,7 @@ struct cbg_handle {
     // basis and vectors
     unsigned char* V = nullptr;
     double *w = nullptr, *w1 = nullptr, *w2 = nullptr, *r = nullptr, *tmp = nullptr, *z = nullptr;
-    double* wdf = nullptr;    // w (then w1) split into FP32 pairs for the DF32 dot kernel (float2[ld])
+    double* wdf = nullptr;    // w (then w1) split into FP32 hi[ld] and lo[ld] planes for the DF32 dot
     double *bdev = nullptr, *xdev = nullptr;   // staging for cbgmres_solve_host
     double* scratch = nullptr;                 // small reductions
     // solver state
@@ -272,6 +287,8 @@ struct cbg_handle {
     int* flag_dev = nullptr;
     long long hist_alloc = 0;
     int grid_dot = 0, grid_axpy = 0, grid_store = 0, grid_spmv = 0, group = 1, gridmax = 0;
+    int grid_tma = 0;         // bulk-copy pipelined basis kernels: one block per SM
+    bool use_tma = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> step_ev;
     // launch accounting and optional per-kernel profiling
@@ -402,7 +419,7 @@ void enqueue_step(cbg_handle* h, int j)
     cudaStream_t s = h->stream;
     const int* active = &h->d.st->active;
     const unsigned char* Vj = h->V + (long long)j * h->ldb;
-    float2* wdf = h->opt.arith == CBG_ARITH_DF32 ? reinterpret_cast<float2*>(h->wdf) : nullptr;
+    float* wdf = h->opt.arith == CBG_ARITH_DF32 ? reinterpret_cast<float*>(h->wdf) : nullptr;
     // steps 3-4: w = A M^{-1} v_j, omega
     {
         SpmvArgs a = spmv_args(h);
@@ -420,12 +437,14 @@ void enqueue_step(cbg_handle* h, int j)
             b2.xscale = 1.0;
             b2.y = h->w;
             b2.ydf = wdf;
+            b2.ydf_ld = h->ld;
             b2.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
         } else {
             a.val = h->valp ? h->valp : h->val;
             a.y = h->w;
             a.ydf = wdf;
+            a.ydf_ld = h->ld;
             a.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
         }
@@ -446,7 +465,13 @@ void enqueue_step(cbg_handle* h, int j)
     da.wdf = wdf;
     da.counter = h->d.counters + 2;
     da.out = h->d.h;
-    launch(h, 0, pass_bytes, [&] { op.dot(h->opt.arith, h->grid_dot, s, da); });
+    // DF32: the bulk-copy pipelined dot (one block per SM); FP64 keeps the register kernel
+    auto run_dot = [&] {
+        if (h->use_tma) op.dot_tma(h->grid_tma, s, da, &h->d.st->fault);
+        else op.dot(h->opt.arith, h->grid_dot, s, da);
+    };
+    auto run_axpy = [&](const AxpyArgs& xa) { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); };
+    launch(h, 0, pass_bytes, run_dot);
 
     AxpyArgs xa{};
     xa.V = h->V;
@@ -464,19 +489,19 @@ void enqueue_step(cbg_handle* h, int j)
     xa.st = h->d.st;
     xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
     xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
-    launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
+    launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
     if (reorth) {
         // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
         da.w = h->w1;
         da.counter = h->d.counters + 3;
         da.out = h->d.u;
-        launch(h, 0, pass_bytes, [&] { op.dot(h->opt.arith, h->grid_dot, s, da); });
+        launch(h, 0, pass_bytes, run_dot);
         xa.coef = h->d.u;
         xa.w_in = h->w1;
         xa.w_out = h->w2;
         xa.wdf_out = nullptr;
         xa.counter = h->d.counters + 5;
-        launch(h, 1, pass_bytes, [&] { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); });
+        launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
     }
     // steps 6, 12-14 and the Givens update
     StoreArgs sa{};
@@ -521,9 +546,10 @@ void enqueue_cycle_end(cbg_handle* h, double* x)
     xa.sign = 1.0;
     xa.nrows = h->ld;
     xa.n = h->n;
+    auto run_axpy = [&](int epi) { op.axpy(h->opt.arith, epi, h->grid_axpy, s, xa); };
     if (h->opt.precond == CBG_PC_SPAI) {
         xa.w_out = h->tmp;
-        launch(h, 4, 0.0, [&] { op.axpy(h->opt.arith, EPI_PLAIN, h->grid_axpy, s, xa); });       // t = V y
+        launch(h, 4, 0.0, [&] { run_axpy(EPI_PLAIN); });                                          // t = V y
         SpmvArgs a = spmv_args(h);
         a.val = h->pvals;
         a.x = h->tmp;
@@ -533,7 +559,7 @@ void enqueue_cycle_end(cbg_handle* h, double* x)
     } else {
         xa.w_out = x;
         xa.dinv = h->opt.precond == CBG_PC_JACOBI ? h->dinv : nullptr;
-        launch(h, 4, 0.0, [&] { op.axpy(h->opt.arith, EPI_XUPD, h->grid_axpy, s, xa); });        // x += D^{-1} V y
+        launch(h, 4, 0.0, [&] { run_axpy(EPI_XUPD); });                                           // x += D^{-1} V y
     }
 }
 
@@ -545,6 +571,7 @@ int read_state(cbg_handle* h, DevState* out)
 {
     CBG_CUDA(cudaMemcpyAsync(out, h->d.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     CBG_CUDA(cudaStreamSynchronize(h->stream));
+    if (out->fault) return CBG_ERR_TIMEOUT;   // a pipelined kernel stopped waiting
     return CBG_OK;
 }
 
@@ -801,7 +828,11 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->grid_axpy = std::max(1, h->grid_axpy);
     h->grid_store = std::max(1, h->grid_store);
     h->grid_spmv = std::max(1, h->grid_spmv);
-    h->gridmax = std::max(std::max(h->grid_dot, h->grid_axpy), std::max(h->grid_store, h->grid_spmv));
+    h->grid_tma = sms;
+    h->use_tma = o.arith == CBG_ARITH_DF32;
+    if (o.arith == CBG_ARITH_DF32 && !op.tma_fits()) TRY(CBG_ERR_UNSUPPORTED);
+    h->gridmax = std::max(std::max(std::max(h->grid_dot, h->grid_axpy), std::max(h->grid_store, h->grid_spmv)),
+                          h->grid_tma);
 
     // state block: DevState + H, R, cs, sn, g, y, h, u, scales + partials + counters
     const int m = restart, ldh = m + 1;
@@ -1062,15 +1093,18 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
         return CBG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const Ops& op = ops_for(fmt);
-    int grid = (int)std::min<long long>(ld / DOT_MIN_ROWS, (long long)num_sms() * std::max(1, op.occ_dot()));
-    double *part = nullptr, *sc = nullptr, *out = nullptr;
-    unsigned int* cnt = nullptr;
+    const bool tma = arith == CBG_ARITH_DF32;
+    int grid = tma ? num_sms()
+                   : (int)std::min<long long>(ld / DOT_MIN_ROWS, (long long)num_sms() * std::max(1, op.occ_dot()));
+    double *part = nullptr, *sc = nullptr, *out = nullptr, *wdf = nullptr;
+    unsigned int* cnt = nullptr;   // [0] last-block counter, [1] fault flag
     int rc = dalloc(&part, (size_t)grid * MAXCOLS);
     if (!rc) rc = dalloc(&sc, ncols);
     if (!rc) rc = dalloc(&out, ncols);
-    if (!rc) rc = dalloc(&cnt, 1);
+    if (!rc) rc = dalloc(&cnt, 2);
+    if (!rc && tma) rc = dalloc(&wdf, ld);
     if (!rc) {
-        cudaMemsetAsync(cnt, 0, sizeof(unsigned int), s);
+        cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), s);
         cudaMemcpyAsync(sc, scales, ncols * sizeof(double), cudaMemcpyHostToDevice, s);
         DotArgs a{};
         a.V = (const unsigned char*)V;
@@ -1082,13 +1116,24 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
         a.part = part;
         a.counter = cnt;
         a.out = out;
-        op.dot(arith, grid, s, a);
+        if (tma) {
+            k_split_df<<<(int)std::min<long long>((ld + THREADS - 1) / THREADS, 4096), THREADS, 0, s>>>(
+                w, ld, reinterpret_cast<float*>(wdf));
+            a.wdf = reinterpret_cast<const float*>(wdf);
+            op.dot_tma(grid, s, a, reinterpret_cast<int*>(cnt + 1));
+        } else {
+            op.dot(arith, grid, s, a);
+        }
+        unsigned int flags[2] = {0u, 0u};
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(hout, out, ncols * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(flags, cnt, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             rc = CBG_ERR_CUDA;
+        else if (flags[1])
+            rc = CBG_ERR_TIMEOUT;
     }
-    cudaFree(part); cudaFree(sc); cudaFree(out); cudaFree(cnt);
+    cudaFree(part); cudaFree(sc); cudaFree(out); cudaFree(cnt); cudaFree(wdf);
     return rc;
 }
 
