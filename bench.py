@@ -126,10 +126,21 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(vals: dict, device) -> dict:
+    """Element-wise maximum of per-rank timings over all ranks of the process group (the
+    slowest replica decides a whole-job time).  Keys must be the same on every rank."""
+    import torch
+    import torch.distributed as dist
+    keys = sorted(vals)
+    t = torch.tensor([float(vals[k]) for k in keys], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return {k: float(t[i]) for i, k in enumerate(keys)}
+
+
 def ncu_traffic_per_element(fmt: str):
     """DRAM bytes per basis element of the basis-GEMV kernels from the committed ncu
-    summary (profiles/basis_gemv_ncu.md, line `traffic_bytes_per_element <cls> <fmt> <x>`)."""
-    path = os.path.join(ROOT, "profiles", "basis_gemv_ncu.md")
+    summary (profiles/basis_gemv_convdiff96.md, line `traffic_bytes_per_element <cls> <fmt> <x>`)."""
+    path = os.path.join(ROOT, "profiles", "basis_gemv_convdiff96.md")
     out = {}
     try:
         with open(path) as f:
@@ -532,9 +543,7 @@ def main():
     launches = sum(r[f][2]["kernel_launches"] for r in runs for f in fmts)
     t_fmt = {f: sum(v) / len(v) for f, v in per_fmt.items()}
     if world > 1:
-        t = torch.tensor([t_fmt[f] for f in fmts], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_fmt = {f: float(t[i]) for i, f in enumerate(fmts)}
+        t_fmt = max_over_ranks(t_fmt, "cuda")
     speedup = {f: t_fmt["f64"] / t_fmt[f] for f in fmts}
     value = speedup[args.headline]
 
@@ -556,7 +565,9 @@ def main():
             p = prof[f][c]
             if p["ms"] > 0:
                 gemv[f"{f}/{c}"] = round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1)
-    roofline = {"bound": "hbm", "kernel": f"k_basis_{cls.split('_')[1]} ({args.headline}, {args.arith})",
+    kname = {"basis_dot": "k_basis_dot_tma" if args.arith == "df32" else "k_basis_dot",
+             "basis_axpy": "k_basis_axpy"}[cls]
+    roofline = {"bound": "hbm", "kernel": f"{kname} ({args.headline}, {args.arith})",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -579,9 +590,7 @@ def main():
                 ts.append(time.perf_counter() - t0)
             te[f] = sum(ts) / len(ts)
         if world > 1:
-            t = torch.tensor([te["f64"], te[args.headline]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = {"f64": float(t[0]), args.headline: float(t[1])}
+            te = max_over_ranks({"f64": te["f64"], args.headline: te[args.headline]}, "cuda")
         e2e = {"value": te["f64"] / te[args.headline], "unit": "x",
                "h2d_bytes_per_step": 2 * 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n,
                "seconds": {k: round(v, 4) for k, v in te.items()}}
