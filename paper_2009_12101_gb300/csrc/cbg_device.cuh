@@ -187,6 +187,26 @@ __device__ __forceinline__ double f32_to_f64_exact(float f)
     return (double)f;
 }
 
+// FP64 -> FP32 with round-to-nearest-even, in integer operations when the result is a
+// normal float or zero (the FP64->FP32 conversion instruction runs on GB300's narrow FP64
+// pipe); subnormal results, overflow, Inf and NaN take the hardware conversion.  A carry
+// out of the rounded significand moves into the exponent, as IEEE rounding does.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+    const unsigned int e = (unsigned int)(u >> 52) & 0x7FFu;
+    if (e - 897u <= 253u) {                                    // 897 <= e <= 1150
+        const unsigned long long m = u & 0xFFFFFFFFFFFFFull;   // 52 fraction bits
+        unsigned int b = ((e - 896u) << 23) | (unsigned int)(m >> 29);
+        const unsigned int rem = (unsigned int)m & 0x1FFFFFFFu, half = 0x10000000u;
+        b += (rem > half || (rem == half && (b & 1u))) ? 1u : 0u;
+        return __uint_as_float(b | sign);
+    }
+    if ((u << 1) == 0ull) return __uint_as_float(sign);       // +-0
+    return __double2float_rn(x);
+}
+
 // hi + lo rounded once to FP64: both widened exactly with integer operations, then one
 // FP64 addition
 __device__ __forceinline__ double df_to_double(float hi, float lo)
@@ -334,7 +354,7 @@ template <int FMT> __device__ __forceinline__ void encode_store(void* base, int6
     if constexpr (FMT == F64) {
         reinterpret_cast<double*>(base)[i] = v;
     } else if constexpr (FMT == F32) {
-        reinterpret_cast<float*>(base)[i] = __double2float_rn(v);
+        reinterpret_cast<float*>(base)[i] = f64_to_f32_rn(v);
     } else if constexpr (FMT == F16) {
         reinterpret_cast<__half*>(base)[i] = __double2half(v);
     } else if constexpr (FMT == I32 || FMT == I16) {
@@ -346,11 +366,11 @@ template <int FMT> __device__ __forceinline__ void encode_store(void* base, int6
         if constexpr (FMT == I32) reinterpret_cast<int*>(base)[i] = q;
         else reinterpret_cast<short*>(base)[i] = (short)q;
     } else if constexpr (FMT == BF16) {
-        float f = __double2float_rn(__dmul_rn(v, p.inv));
+        float f = f64_to_f32_rn(__dmul_rn(v, p.inv));
         __nv_bfloat16 b = __float2bfloat16_rn(f);
         reinterpret_cast<__nv_bfloat16*>(base)[i] = b;
     } else if constexpr (FMT == E4M3) {
-        float f = __double2float_rn(__dmul_rn(v, p.inv));
+        float f = f64_to_f32_rn(__dmul_rn(v, p.inv));
         reinterpret_cast<unsigned char*>(base)[i] =
             (unsigned char)__nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3);
     }

@@ -533,11 +533,11 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 2 ? 3 : 2) k_b
 }
 
 // ========================================== store v_{j+1} = w / h_{j+1,j} (steps 6, 12-14)
-// Every block reduces the per-block norm partials of the preceding axpy (cheap and
-// deterministic), forms h_{j+1,j}, 1/h and max|v|, and encodes its rows into column
-// `col`.  Block 0 additionally completes the Hessenberg column j (h from pass 1 plus u
-// from pass 2), applies the Givens rotations (Section 2), updates g, writes the
-// residual history and decides whether the cycle continues.
+// Every block reads the norms finalised by the preceding axpy, forms h_{j+1,j}, 1/h and
+// the format's scale, and encodes its rows into column `col`.  The last block to finish
+// additionally completes the Hessenberg column j (h from pass 1 plus u from pass 2),
+// applies the Givens rotations (Section 2), updates g, writes the residual history and
+// decides whether the cycle continues.
 // mode 0: Arnoldi step (finalize + store column j+1); mode 1: first vector of a cycle
 // (w = r0, norms from the residual kernel, no Hessenberg work).
 struct StoreArgs {
@@ -550,13 +550,22 @@ struct StoreArgs {
     int reorth;               // pass 2 ran (h += u)
     long long n;
     int fmt;
+    unsigned int* counter;    // last-block counter (mode 0: the last block runs the finalize)
 };
 
 
-// Executed by warp 0 of block 0.  The column, the previous rotations and the
-// coefficients are staged in shared memory by the whole warp first, so lane 0's
-// sequential rotation chain runs at shared-memory latency.
-static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* sR, double* scs, double* ssn)
+// Executed by warp 0 of the store kernel's last block.  The column, the previous
+// rotations and the coefficients are staged in shared memory by the whole warp first.
+//
+// Applying the j previous rotations to the new column is a first-order linear recurrence
+// in the carried entry x (x_0 = h_0, x_{i+1} = -s_i x_i + c_i h_{i+1}, rotated entry
+// R_i = c_i x_i + s_i h_{i+1}).  GB300's FP64 unit has a long latency, so instead of a
+// j-long dependent chain the warp evaluates it as a scan of affine maps: each lane
+// composes the maps of a contiguous chunk of rotations, an exclusive warp scan composes
+// the chunks, and each lane then replays its chunk from its incoming x.  The chain is
+// 2*ceil(j/32) + 5 compositions long.
+static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* sR, double* sRo, double* scs,
+                                        double* ssn)
 {
     DevState* st = a.d.st;
     const int j = a.j, ldh = st->m + 1;
@@ -576,22 +585,48 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     double* Hc = a.d.H + (long long)j * ldh;
     for (int i = lane; i < ldh; i += 32) Hc[i] = i <= j + 1 ? sR[i] : 0.0;   // raw column
     __syncwarp();
-    if (lane == 0) {
-        double r0 = sR[0];
-        for (int i = 0; i < j; i++) {
-            const double c = scs[i], s = ssn[i], r1 = sR[i + 1];
-            sR[i] = __dadd_rn(__dmul_rn(c, r0), __dmul_rn(s, r1));
-            r0 = __dadd_rn(__dmul_rn(-s, r0), __dmul_rn(c, r1));
+    // chunk [i0, i1) of the rotations for this lane; the rotated entries go to sRo (not in
+    // place: a neighbouring lane still reads the unrotated h_{i+1})
+    const int K = (j + 31) / 32;
+    const int i0 = lane * K < j ? lane * K : j, i1 = i0 + K < j ? i0 + K : j;
+    double A = 1.0, B = 0.0;                 // composite map x -> A x + B of the chunk
+    for (int i = i0; i < i1; i++) {
+        const double ai = -ssn[i], bi = __dmul_rn(scs[i], sR[i + 1]);
+        B = __fma_rn(ai, B, bi);
+        A = __dmul_rn(ai, A);
+    }
+    // exclusive scan of the chunk maps: (A, B) of lanes 0 .. lane-1, composed in order
+    double PA = A, PB = B;                   // inclusive prefix
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double qa = __shfl_up_sync(0xffffffffu, PA, o), qb = __shfl_up_sync(0xffffffffu, PB, o);
+        if (lane >= o) {                     // (PA, PB) o (qa, qb): x -> PA (qa x + qb) + PB
+            PB = __fma_rn(PA, qb, PB);
+            PA = __dmul_rn(PA, qa);
         }
-        sR[j] = r0;
+    }
+    double EA = __shfl_up_sync(0xffffffffu, PA, 1), EB = __shfl_up_sync(0xffffffffu, PB, 1);
+    if (lane == 0) { EA = 1.0; EB = 0.0; }
+    double x = __fma_rn(EA, sR[0], EB);      // carried entry entering this lane's chunk
+    for (int i = i0; i < i1; i++) {
+        const double c = scs[i], sn = ssn[i], h1 = sR[i + 1];
+        sRo[i] = __dadd_rn(__dmul_rn(c, x), __dmul_rn(sn, h1));
+        x = __dadd_rn(__dmul_rn(-sn, x), __dmul_rn(c, h1));
+    }
+    __syncwarp();
+    // the lane that applied rotation j-1 holds the carried entry after all of them
+    const int last = j > 0 ? (j - 1) / K : 0;
+    const double r0all = __shfl_sync(0xffffffffu, x, last);
+    if (lane == 0) {
+        const double r0 = j > 0 ? r0all : sR[0];
         double rr = hypot(r0, hn);
         double c, s;
         if (rr == 0.0) { c = 1.0; s = 0.0; }
         else { c = r0 / rr; s = hn / rr; }
         a.d.cs[j] = c;
         a.d.sn[j] = s;
-        sR[j] = rr;
-        sR[j + 1] = 0.0;
+        sRo[j] = rr;
+        sRo[j + 1] = 0.0;
         double gj = a.d.g[j];
         double gn = __dmul_rn(-s, gj);
         a.d.g[j + 1] = gn;
@@ -616,17 +651,17 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     }
     __syncwarp();
     double* Rc = a.d.R + (long long)j * ldh;
-    for (int i = lane; i < ldh; i += 32) Rc[i] = i <= j + 1 ? sR[i] : 0.0;
+    for (int i = lane; i < ldh; i += 32) Rc[i] = i <= j + 1 ? sRo[i] : 0.0;
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
+__global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
 {
     DevState* st = a.d.st;
     if (st->active == 0) return;
     __shared__ double sh_inv, sh_hn;
     __shared__ EncParams sh_ep;
-    __shared__ double sR[MAXCOLS + 1], scs[MAXCOLS], ssn[MAXCOLS];
+    __shared__ double sR[MAXCOLS + 1], sRo[MAXCOLS + 1], scs[MAXCOLS], ssn[MAXCOLS];
     if (threadIdx.x == 0) {
         // norms of the vector to store: the residual (first vector of a cycle) or the
         // orthogonalised w, both finalised by the last block of the producing kernel
@@ -640,10 +675,7 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
     __syncthreads();
     const double inv = sh_inv;
     const EncParams ep = sh_ep;
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        if (threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
-        if (a.mode == 0) arnoldi_finalize(a, sh_hn, sR, scs, ssn);
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
     const long long stride = (long long)gridDim.x * THREADS;
     for (long long i0 = (long long)blockIdx.x * THREADS + threadIdx.x; i0 < a.n; i0 += 4 * stride) {
         double wv[4];
@@ -658,6 +690,9 @@ __global__ void __launch_bounds__(THREADS) k_store(StoreArgs a)
             if (i < a.n) encode_store<FMT>(a.Vcol, i, __dmul_rn(wv[q], inv), ep);
         }
     }
+    // The Hessenberg / Givens work is a serial chain of FP64 operations; it runs in the
+    // last block to finish, when no other block competes for the SM's narrow FP64 pipe.
+    if (a.mode == 0 && last_block(a.counter) && threadIdx.x < 32) arnoldi_finalize(a, sh_hn, sR, sRo, scs, ssn);
 }
 
 // ======================================================= SpMV with on-the-fly decode
@@ -696,7 +731,34 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     const long long gid = ((long long)blockIdx.x * THREADS + threadIdx.x) / GROUP;
     const long long ngroups = (long long)gridDim.x * THREADS / GROUP;
     const double xs = a.xscale_dev ? *a.xscale_dev : a.xscale;
-    double ss = 0.0, mx = 0.0;
+    double ss = 0.0;
+    unsigned long long mxb = 0;
+    auto xval = [&](int c) -> double {
+        if constexpr (XFMT < 0) return reinterpret_cast<const double*>(a.x)[c];
+        else return code_value<XFMT>(a.x, c);
+    };
+    // row epilogue: scale, residual / accumulate, store (and the split copy), norms
+    auto finish = [&](long long row, double s) {
+        if constexpr (XFMT >= 0) {
+            if (xs != 1.0) s = __dmul_rn(s, xs);   // unit scale (float formats): no FP64 op
+        }
+        double yv = s;
+        if constexpr (MODE == SPMV_RESIDUAL) yv = __dsub_rn(a.b[row], s);
+        if constexpr (MODE == SPMV_ACCUM) yv = __dadd_rn(a.y[row], s);
+        a.y[row] = yv;
+        if constexpr (MODE == SPMV_ARNOLDI) {
+            if (a.ydf) {
+                float h, l;
+                split_f64(yv, h, l);
+                a.ydf[row] = h;
+                a.ydf[a.ydf_ld + row] = l;
+            }
+        }
+        ss = __fma_rn(yv, yv, ss);
+        // max |y| on the bit patterns of non-negative doubles (integer pipe)
+        const unsigned long long ab = (unsigned long long)__double_as_longlong(yv) & 0x7FFFFFFFFFFFFFFFull;
+        mxb = ab > mxb ? ab : mxb;
+    };
     for (long long row = gid;; row += ngroups) {
         const bool valid = row < a.n;
         if constexpr (GROUP > 1) {
@@ -706,41 +768,20 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
         }
         const int p0 = valid ? a.rowptr[row] : 0, p1 = valid ? a.rowptr[row + 1] : 0;
         double s = 0.0;
-        for (int p = p0 + lane_g; p < p1; p += GROUP) {
-            const int c = a.col[p];
-            double xv;
-            if constexpr (XFMT < 0) xv = reinterpret_cast<const double*>(a.x)[c];
-            else xv = code_value<XFMT>(a.x, c);
-            s = __fma_rn(a.val[p], xv, s);
-        }
+        for (int p = p0 + lane_g; p < p1; p += GROUP) s = __fma_rn(a.val[p], xval(a.col[p]), s);
         if constexpr (GROUP > 1) {
 #pragma unroll
             for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
         }
-        if constexpr (XFMT >= 0) s = __dmul_rn(s, xs);
-        if (valid && lane_g == 0) {
-            double yv = s;
-            if constexpr (MODE == SPMV_RESIDUAL) yv = __dsub_rn(a.b[row], s);
-            if constexpr (MODE == SPMV_ACCUM) yv = __dadd_rn(a.y[row], s);
-            a.y[row] = yv;
-            if constexpr (MODE == SPMV_ARNOLDI) {
-                if (a.ydf) {
-                    float h, l;
-                    split_f64(yv, h, l);
-                    a.ydf[row] = h;
-                    a.ydf[a.ydf_ld + row] = l;
-                }
-            }
-            ss = __fma_rn(yv, yv, ss);
-            mx = fmax(mx, fabs(yv));
-        }
+        if (valid && lane_g == 0) finish(row, s);
     }
+    const double mx = __longlong_as_double((long long)mxb);
     if constexpr (MODE == SPMV_PLAIN || MODE == SPMV_ACCUM) return;
     else {
         ss = warp_sum(ss);
-        mx = warp_max(mx);
+        const double mxw = warp_max(mx);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mx; }
+        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mxw; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0, m = 0.0;

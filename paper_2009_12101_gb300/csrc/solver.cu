@@ -514,6 +514,7 @@ void enqueue_step(cbg_handle* h, int j)
     sa.reorth = reorth ? 1 : 0;
     sa.n = h->n;
     sa.fmt = h->fmt;
+    sa.counter = h->d.counters + 6;
     launch(h, 3, store_bytes(h), [&] { op.store(h->grid_store, s, sa); });
 }
 
@@ -821,7 +822,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->grid_dot = (int)std::min<long long>(h->ld / DOT_MIN_ROWS, (long long)sms * occ_dot);
     const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
     h->grid_axpy = (int)std::min<long long>(axpy_blocks, (long long)sms * occ_axpy);
-    h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 8);
+    h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
     h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
     h->grid_spmv = (int)std::min<long long>((n * h->group + THREADS - 1) / THREADS, (long long)sms * occ_spmv);
     h->grid_dot = std::max(1, h->grid_dot);

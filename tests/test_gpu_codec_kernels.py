@@ -37,6 +37,30 @@ def test_encode_decode_bit_exact(fmt, n):
     assert np.array_equal(dec_g, dec_o)
 
 
+def test_f32_encode_rounding_edges():
+    """The f32 encoder rounds FP64 -> FP32 to nearest even with integer operations on the
+    normal range; check ties, neighbours of ties, the normal/subnormal boundary, the
+    overflow boundary and special values against numpy's correctly rounded cast."""
+    torch, cb = need_gpu()
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal(2000).astype(np.float32) * np.float32(2.0) ** rng.integers(-120, 120, 2000)
+    f = f[np.isfinite(f) & (f != 0)].astype(np.float64)
+    ulp = np.abs(np.spacing(f.astype(np.float32)).astype(np.float64))
+    ties = f + 0.5 * ulp
+    above = np.nextafter(ties, np.inf)
+    below = np.nextafter(ties, -np.inf)
+    tiny = np.float64(np.finfo(np.float32).tiny)
+    big = np.float64(np.finfo(np.float32).max)
+    edges = np.array([0.0, -0.0, tiny, -tiny, np.nextafter(tiny, 0), tiny * 0.75, tiny * 1e-3, 1e-300,
+                      big, -big, big + 0.49 * np.spacing(np.float32(big)), big * (1 + 2.0 ** -25), 1e300,
+                      np.inf, -np.inf, 1.0, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 1.0 - 2.0 ** -25])
+    v = np.concatenate([f, ties, above, below, -ties, edges])
+    ref = v.astype(np.float32)
+    codes, scale = cb.encode("f32", torch.from_numpy(v).cuda(), 1.0)
+    got = codes.cpu().numpy().view(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), np.count_nonzero(got.view(np.uint32) != ref.view(np.uint32))
+
+
 @pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3", "i16"])
 def test_decode_every_code(fmt):
     """All 2^16 (2^8) codes decode to the oracle's values (finite codes)."""
