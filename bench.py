@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--formats", default="f64,f32,f16,i32,i16")
     p.add_argument("--headline", default="f32")
     p.add_argument("--arith", default="df32")
+    p.add_argument("--precond", default="none", choices=["none", "jacobi", "bj4"],
+                   help="right preconditioner of the conv-diff workload (bj4: block-Jacobi, 4-row blocks)")
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--maxit", type=int, default=40000)
     p.add_argument("--restart", type=int, default=100)
@@ -507,7 +509,8 @@ def main():
     stream = torch.cuda.current_stream()
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
-    solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, profile=True)
+    solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, precond=args.precond,
+                                     profile=True)
                for f in fmts}
 
     def solve_all(record):
@@ -614,7 +617,8 @@ def main():
             "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "df32" if args.arith == "df32" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "nnz": A.nnz, "restart": args.restart,
+            "config": {"workload": WORKLOAD if args.precond == "none" else f"{WORKLOAD}_{args.precond}",
+                       "n": n, "nnz": A.nnz, "restart": args.restart, "precond": args.precond,
                        "tol": args.tol, "headline_format": args.headline, "formats": fmts,
                        "arith": ("basis products in double-float (FP32 pairs), SpMV/norms/Givens/"
                                  "least squares in FP64" if args.arith == "df32" else "all FP64"),

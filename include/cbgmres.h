@@ -42,7 +42,14 @@ typedef enum {
     CBG_I16 = 6    /* fixed point, code = rint(v / sigma), sigma = max|v| / (2^15-1) */
 } cbg_format;
 
-typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2 } cbg_precond;
+/* Right preconditioners M^{-1} (Fig. 1 steps 3 and 17: w = A M^{-1} v, x += M^{-1} V y).
+ * JACOBI: diagonal scaling, folded into the stored values A D^{-1} (Section 5.1).
+ * SPAI:   z = P v with P on A's pattern (cbgmres_set_spai; the learned preconditioner).
+ * BJ4:    block-Jacobi with diagonal blocks of 4 consecutive rows (the last block may be
+ *         smaller), each inverted in FP64 with partial pivoting at create (Section 5.5,
+ *         block size 4); applied as z = D^{-1} v before the SpMV.  A singular block makes
+ *         cbgmres_create fail with CBG_ERR_ARG. */
+typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2, CBG_PC_BJ4 = 3 } cbg_precond;
 typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
 
 /* Arithmetic of the basis products (Fig. 1 steps 5, 8, 17).

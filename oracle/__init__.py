@@ -32,7 +32,7 @@ F64, F32, F16, BF16, E4M3, I32, I16 = range(7)
 FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "e4m3": E4M3, "i32": I32, "i16": I16}
 CODE_DTYPE = {F64: np.float64, F32: np.float32, F16: np.uint16, BF16: np.uint16,
               E4M3: np.uint8, I32: np.int32, I16: np.int16}
-PC_NONE, PC_JACOBI, PC_SPAI = 0, 1, 2
+PC_NONE, PC_JACOBI, PC_SPAI, PC_BJ4 = 0, 1, 2, 3
 REORTH_ALWAYS, REORTH_CONDITIONAL, REORTH_NEVER = 0, 1, 2
 OK, NOT_CONVERGED, ERR_ARG, ERR_NONFINITE = 0, 1, -1, -2
 

@@ -270,7 +270,50 @@ typedef struct {
     int precond;
     const double* dinv_src;   /* diagonal of A (Jacobi) */
     const double* pvals;      /* SPAI values          */
+    const double* binv;       /* block-Jacobi: inverse of diagonal block b, row-major 4x4 at 16 b */
 } problem;
+
+/* Inverse of the diagonal blocks of A (rows and columns 4b .. 4b+3, the last block
+ * possibly smaller) by Gauss-Jordan elimination on [D | I] with partial pivoting (the
+ * largest |entry| of the column at or below the diagonal).  Returns 0, or -1 if a block
+ * is singular. */
+static int block_jacobi_inverse(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                                double* binv)
+{
+    for (int64_t r0 = 0; r0 < n; r0 += 4) {
+        const int kb = (int)(n - r0 < 4 ? n - r0 : 4);
+        double aug[4][8];
+        for (int i = 0; i < kb; i++) {
+            for (int c = 0; c < 2 * kb; c++) aug[i][c] = (c == kb + i) ? 1.0 : 0.0;
+            for (int32_t p = rowptr[r0 + i]; p < rowptr[r0 + i + 1]; p++) {
+                const int64_t c = col[p] - r0;
+                if (c >= 0 && c < kb) aug[i][c] = val[p];
+            }
+        }
+        for (int k = 0; k < kb; k++) {
+            int piv = k;
+            for (int i = k + 1; i < kb; i++)
+                if (fabs(aug[i][k]) > fabs(aug[piv][k])) piv = i;
+            if (aug[piv][k] == 0.0) return -1;
+            for (int c = 0; c < 2 * kb; c++) {
+                const double t = aug[k][c];
+                aug[k][c] = aug[piv][c];
+                aug[piv][c] = t;
+            }
+            const double d = aug[k][k];
+            for (int c = 0; c < 2 * kb; c++) aug[k][c] = aug[k][c] / d;
+            for (int i = 0; i < kb; i++) {
+                if (i == k) continue;
+                const double f = aug[i][k];
+                for (int c = 0; c < 2 * kb; c++) aug[i][c] = aug[i][c] - f * aug[k][c];
+            }
+        }
+        double* B = binv + 16 * (r0 / 4);
+        for (int i = 0; i < kb; i++)
+            for (int c = 0; c < kb; c++) B[4 * i + c] = aug[i][kb + c];
+    }
+    return 0;
+}
 
 /* z = M^{-1} v  (Fig. 1 step 3 and step 17; right preconditioning) */
 static void apply_precond(const problem* P, const double* v, double* z)
@@ -280,6 +323,16 @@ static void apply_precond(const problem* P, const double* v, double* z)
         for (int64_t i = 0; i < n; i++) z[i] = v[i] / P->dinv_src[i];
     } else if (P->precond == OR_PC_SPAI) {
         or_spmv(n, P->rowptr, P->col, P->pvals, v, z);
+    } else if (P->precond == OR_PC_BJ4) {
+        for (int64_t r0 = 0; r0 < n; r0 += 4) {
+            const int kb = (int)(n - r0 < 4 ? n - r0 : 4);
+            const double* B = P->binv + 16 * (r0 / 4);
+            for (int i = 0; i < kb; i++) {
+                double s = 0.0;
+                for (int c = 0; c < kb; c++) s += B[4 * i + c] * v[r0 + c];
+                z[r0 + i] = s;
+            }
+        }
     } else {
         memcpy(z, v, (size_t)n * sizeof(double));
     }
@@ -322,15 +375,21 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         return a->status;
     }
 
-    problem P = {n, rowptr, col, val, a->precond, NULL, a->pvals};
+    problem P = {n, rowptr, col, val, a->precond, NULL, a->pvals, NULL};
     double* diag = NULL;
+    double* binv = NULL;
+    if (a->precond == OR_PC_BJ4) {
+        binv = (double*)calloc((size_t)(16 * ((n + 3) / 4)), sizeof(double));
+        if (!binv || block_jacobi_inverse(n, rowptr, col, val, binv)) { free(binv); return a->status; }
+        P.binv = binv;
+    }
     if (a->precond == OR_PC_JACOBI) {
         diag = (double*)calloc((size_t)n, sizeof(double));
         for (int64_t i = 0; i < n; i++)
             for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++)
                 if (col[p] == i) diag[i] = val[p];
         for (int64_t i = 0; i < n; i++)
-            if (diag[i] == 0.0) { free(diag); return a->status; }
+            if (diag[i] == 0.0) { free(diag); free(binv); return a->status; }
         P.dinv_src = diag;
     }
 
@@ -339,6 +398,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         for (int64_t i = 0; i < n; i++) x[i] = 0.0;
         a->status = OR_OK;
         free(diag);
+        free(binv);
         return a->status;
     }
     const double target = a->tol * bnorm;
@@ -482,7 +542,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
     }
 done:
     free(V); free(codes); free(r); free(w); free(z); free(tmp); free(H); free(R);
-    free(cs); free(sn); free(g); free(h); free(u); free(y); free(diag);
+    free(cs); free(sn); free(g); free(h); free(u); free(y); free(diag); free(binv);
     return a->status;
 }
 

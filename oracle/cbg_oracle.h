@@ -52,7 +52,8 @@ extern "C" {
 /* storage formats of the Krylov basis */
 enum { OR_F64 = 0, OR_F32 = 1, OR_F16 = 2, OR_BF16 = 3, OR_E4M3 = 4, OR_I32 = 5, OR_I16 = 6 };
 /* preconditioners (right preconditioning, Fig. 1 step 3 / step 17) */
-enum { OR_PC_NONE = 0, OR_PC_JACOBI = 1, OR_PC_SPAI = 2 };
+enum { OR_PC_NONE = 0, OR_PC_JACOBI = 1, OR_PC_SPAI = 2,
+       OR_PC_BJ4 = 3 /* block-Jacobi, blocks of 4 consecutive rows (Section 5.5) */ };
 /* re-orthogonalisation modes (Fig. 1 steps 7-11) */
 enum { OR_REORTH_ALWAYS = 0, OR_REORTH_CONDITIONAL = 1, OR_REORTH_NEVER = 2 };
 /* status codes */

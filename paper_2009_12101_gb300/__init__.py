@@ -22,7 +22,7 @@ from .build import build as _build
 
 FORMATS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "i32": 5, "i16": 6}
 FORMAT_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i16": 2}
-PRECONDS = {"none": 0, "jacobi": 1, "spai": 2}
+PRECONDS = {"none": 0, "jacobi": 1, "spai": 2, "bj4": 3}
 REORTH = {"always": 0, "conditional": 1, "never": 2}
 ARITH = {"df32": 0, "fp64": 1}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "STAGNATED", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM",

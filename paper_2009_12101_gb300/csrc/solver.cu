@@ -120,6 +120,60 @@ __global__ void k_jacobi_prepare(const int* rowptr, const int* col, const double
     }
 }
 
+// Block-Jacobi with blocks of BJ rows (Section 5.5 uses block size 4): one thread per
+// diagonal block extracts it from A, inverts it by Gauss-Jordan elimination with partial
+// pivoting in FP64, and writes its rows of P = D^{-1} as a CSR matrix (rows of a full
+// block hold BJ entries, the last block's rows hold its size).  A zero pivot (singular
+// block) or a non-finite inverse sets *bad.
+constexpr int BJ = 4;
+__global__ void k_bj_setup(const int* rowptr, const int* col, const double* val, long long n, int* prow,
+                           int* pcol, double* pval, int* bad)
+{
+    const long long nb = (n + BJ - 1) / BJ, nfull = n / BJ;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        const long long r0 = b * BJ;
+        const int kb = (int)(n - r0 < BJ ? n - r0 : BJ);
+        double M[BJ][2 * BJ];
+        for (int i = 0; i < kb; i++) {
+            for (int k = 0; k < 2 * BJ; k++) M[i][k] = (k == kb + i) ? 1.0 : 0.0;
+            for (int p = rowptr[r0 + i]; p < rowptr[r0 + i + 1]; p++) {
+                const long long c = col[p] - r0;
+                if (c >= 0 && c < kb) M[i][c] = val[p];
+            }
+        }
+        bool ok = true;
+        for (int k = 0; k < kb && ok; k++) {
+            int piv = k;
+            for (int i = k + 1; i < kb; i++)
+                if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
+            if (M[piv][k] == 0.0) { ok = false; break; }
+            if (piv != k)
+                for (int c = 0; c < 2 * kb; c++) { const double t = M[k][c]; M[k][c] = M[piv][c]; M[piv][c] = t; }
+            const double inv = 1.0 / M[k][k];
+            for (int c = 0; c < 2 * kb; c++) M[k][c] = __dmul_rn(M[k][c], inv);
+            for (int i = 0; i < kb; i++) {
+                if (i == k) continue;
+                const double f = M[i][k];
+                if (f != 0.0)
+                    for (int c = 0; c < 2 * kb; c++) M[i][c] = __fma_rn(-f, M[k][c], M[i][c]);
+            }
+        }
+        for (int i = 0; i < kb; i++) {
+            const long long row = r0 + i;
+            const long long q = row < nfull * BJ ? row * BJ : nfull * BJ * BJ + (long long)(row - nfull * BJ) * kb;
+            prow[row] = (int)q;
+            for (int c = 0; c < kb; c++) {
+                const double v = ok ? M[i][kb + c] : 0.0;
+                if (!isfinite(v)) ok = false;
+                pcol[q + c] = (int)(r0 + c);
+                pval[q + c] = v;
+            }
+        }
+        if (!ok) atomicExch(bad, 1);
+        if (b == nb - 1) prow[n] = (int)(nfull * BJ * BJ + (long long)(n - nfull * BJ) * (n - nfull * BJ));
+    }
+}
+
 __global__ void k_scale_columns(const int* col, const double* val, const double* dinv, long long nnz, double* out)
 {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x)
@@ -273,7 +327,10 @@ struct cbg_handle {
     double* val = nullptr;     // A
     double* valp = nullptr;    // A D^{-1} (Jacobi) or nullptr
     double* dinv = nullptr;    // D^{-1}
-    double* pvals = nullptr;   // SPAI values (A's pattern)
+    double* pvals = nullptr;   // values of P: SPAI (A's pattern) or block-Jacobi inverse blocks
+    int* prow = nullptr;       // P's pattern: A's for SPAI, the diagonal blocks for block-Jacobi
+    int* pcol = nullptr;
+    bool own_ppat = false;
     // basis and vectors
     unsigned char* V = nullptr;
     double *w = nullptr, *w1 = nullptr, *w2 = nullptr, *r = nullptr, *tmp = nullptr, *z = nullptr;
@@ -306,6 +363,7 @@ void free_handle(cbg_handle* h)
 {
     if (!h) return;
     cudaFree(h->rowptr); cudaFree(h->col); cudaFree(h->val); cudaFree(h->valp); cudaFree(h->dinv);
+    if (h->own_ppat) { cudaFree(h->prow); cudaFree(h->pcol); }
     cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->wdf); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
     cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
     cudaFree(h->state_block); cudaFree(h->d.hist);
@@ -426,7 +484,9 @@ void enqueue_step(cbg_handle* h, int j)
         a.active = active;
         a.xscale_dev = h->d.scales + j;
         a.x = Vj;
-        if (h->opt.precond == CBG_PC_SPAI) {
+        if (h->opt.precond == CBG_PC_SPAI || h->opt.precond == CBG_PC_BJ4) {
+            a.rowptr = h->prow;
+            a.col = h->pcol;
             a.val = h->pvals;
             a.y = h->z;
             launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_PLAIN, h->group, h->grid_spmv, s, a); });   // z = P v
@@ -548,10 +608,12 @@ void enqueue_cycle_end(cbg_handle* h, double* x)
     xa.nrows = h->ld;
     xa.n = h->n;
     auto run_axpy = [&](int epi) { op.axpy(h->opt.arith, epi, h->grid_axpy, s, xa); };
-    if (h->opt.precond == CBG_PC_SPAI) {
+    if (h->opt.precond == CBG_PC_SPAI || h->opt.precond == CBG_PC_BJ4) {
         xa.w_out = h->tmp;
         launch(h, 4, 0.0, [&] { run_axpy(EPI_PLAIN); });                                          // t = V y
         SpmvArgs a = spmv_args(h);
+        a.rowptr = h->prow;
+        a.col = h->pcol;
         a.val = h->pvals;
         a.x = h->tmp;
         a.xscale = 1.0;
@@ -744,7 +806,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     if (opt) o = *opt;
     else cbgmres_options_default(&o);
     if (o.arith != CBG_ARITH_DF32 && o.arith != CBG_ARITH_FP64) return CBG_ERR_ARG;
-    if (o.precond < CBG_PC_NONE || o.precond > CBG_PC_SPAI) return CBG_ERR_ARG;
+    if (o.precond < CBG_PC_NONE || o.precond > CBG_PC_BJ4) return CBG_ERR_ARG;
     if (o.reorth == CBG_REORTH_CONDITIONAL) return CBG_ERR_UNSUPPORTED;
     if (o.reorth < CBG_REORTH_ALWAYS || o.reorth > CBG_REORTH_NEVER) return CBG_ERR_ARG;
     if (o.spmv_group != 0 && (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
@@ -801,6 +863,22 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         cudaMemset(bad, 0, sizeof(int));
         k_jacobi_prepare<<<1024, 256>>>(h->rowptr, h->col, h->val, n, h->dinv, bad);
         k_scale_columns<<<2048, 256>>>(h->col, h->val, h->dinv, nnz, h->valp);
+        int hbad = 0;
+        if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        if (hbad) TRY(CBG_ERR_ARG);
+    }
+    h->prow = h->rowptr;
+    h->pcol = h->col;
+    if (o.precond == CBG_PC_BJ4) {
+        const long long nfull = n / BJ, rest = n - nfull * BJ, pnnz = nfull * BJ * BJ + rest * rest;
+        h->own_ppat = true;
+        TRY(dalloc(&h->prow, n + 1));
+        TRY(dalloc(&h->pcol, pnnz));
+        TRY(dalloc(&h->pvals, pnnz));
+        int* bad = (int*)h->scratch;
+        cudaMemset(bad, 0, sizeof(int));
+        k_bj_setup<<<(int)std::min<long long>((n / BJ + 256) / 256, 4096), 256>>>(h->rowptr, h->col, h->val, n,
+                                                                                  h->prow, h->pcol, h->pvals, bad);
         int hbad = 0;
         if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
         if (hbad) TRY(CBG_ERR_ARG);
@@ -897,7 +975,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
 
 int cbgmres_set_spai(cbg_handle* h, const double* pvals, int on_device)
 {
-    if (!h || !pvals) return CBG_ERR_ARG;
+    if (!h || !pvals || h->opt.precond == CBG_PC_BJ4) return CBG_ERR_ARG;
     if (!h->pvals) {
         int rc = dalloc(&h->pvals, h->nnz);
         if (rc) return rc;

@@ -91,6 +91,39 @@ def test_jacobi_parity():
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
+@pytest.mark.parametrize("fmt", ["f64", "f32", "f16", "i16"])
+@pytest.mark.parametrize("prob", ["convdiff20", "diffusion_cc13"])
+def test_block_jacobi_parity(prob, fmt):
+    """Block-Jacobi with 4-row blocks (Section 5.5): Hessenberg, iterations and x against
+    the oracle's own block inversion; n = 8000 / 2197 (a partial last block)."""
+    torch, cb = need_gpu()
+    A = W.convdiff3d(20) if prob == "convdiff20" else W.diffusion3d_cc(13)[0]
+    xs = W.exact_solution(A.n, 6); b = W.rhs_from_solution(A, xs)
+    ro = O.gmres(A, b, m=40, fmt=O.FORMATS[fmt], precond=O.PC_BJ4, tol=1e-10, maxit=5000, want_H1=True)
+    assert ro["status"] == O.OK
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=40, fmt=fmt, precond="bj4") as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), 10)
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000)
+    assert np.all(col_relerr(Hg, ro["H1"], 10) <= 1e-10)
+    assert st["status"] == 0
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    assert np.linalg.norm(b - O.spmv(A, x)) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
+
+
+def test_block_jacobi_rejects_singular_block():
+    torch, cb = need_gpu()
+    D = np.eye(9)
+    D[4:8, 4:8] = 1.0            # a rank-one diagonal block
+    D[0, 8] = 0.5                # coupling outside the blocks
+    A = W.from_dense(D)
+    with pytest.raises(cb.CbgError) as e:
+        cb.Solver.from_csr(A, restart=5, fmt="f64", precond="bj4")
+    assert e.value.status == -1
+
+
 def test_spai_equal_to_jacobi_when_p_is_diagonal():
     """P = D^{-1} on A's pattern (zeros off the diagonal) is the Jacobi preconditioner."""
     torch, cb = need_gpu()

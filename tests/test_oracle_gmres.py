@@ -298,3 +298,62 @@ def test_paper_protocol_32bit_formats_match_f64(oracle_lib):
         its[fmt] = r["iters"]
     assert its["f64"] <= its["f32"] <= 1.25 * its["f64"]
     assert its["f64"] <= its["i32"] <= 1.25 * its["f64"]
+
+
+# ---------------------------------------------------------------- block-Jacobi (Section 5.5)
+def _block_diag(n, seed):
+    rng = np.random.default_rng(seed)
+    D = np.zeros((n, n))
+    for r0 in range(0, n, 4):
+        k = min(4, n - r0)
+        D[r0:r0 + k, r0:r0 + k] = rng.standard_normal((k, k)) + 3 * np.eye(k)
+    return D
+
+
+@pytest.mark.parametrize("n", [8, 22, 25])
+def test_block_jacobi_exact_on_block_diagonal(n):
+    """A block-diagonal A with 4x4 blocks (last block partial): M^{-1} = A^{-1}, so A M^{-1} = I
+    and GMRES ends after one step with the exact solution."""
+    D = _block_diag(n, n)
+    A = W.from_dense(D)
+    b = np.random.default_rng(1).standard_normal(n)
+    r = O.gmres(A, b, m=10, fmt=O.F64, precond=O.PC_BJ4, tol=1e-12)
+    assert r["status"] == O.OK and r["iters"] == 1
+    assert np.allclose(r["x"], np.linalg.solve(D, b), rtol=1e-12, atol=1e-14)
+
+
+def test_block_jacobi_equals_jacobi_when_blocks_are_diagonal():
+    """If A has no couplings inside its 4-row blocks, block-Jacobi is scalar Jacobi."""
+    rng = np.random.default_rng(3)
+    n = 64
+    M = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.1)
+    blk = np.arange(n) // 4
+    M[blk[:, None] == blk[None, :]] = 0.0
+    M += np.diag(4.0 + rng.random(n))
+    A = W.from_dense(M)
+    b = rng.standard_normal(n)
+    rj = O.gmres(A, b, m=20, fmt=O.F64, precond=O.PC_JACOBI, tol=1e-11)
+    rb = O.gmres(A, b, m=20, fmt=O.F64, precond=O.PC_BJ4, tol=1e-11)
+    assert rj["status"] == rb["status"] == O.OK
+    assert rj["iters"] == rb["iters"]
+    assert np.allclose(rj["x"], rb["x"], rtol=1e-10)
+
+
+def test_block_jacobi_singular_block_is_an_error():
+    D = np.eye(8)
+    D[4:8, 4:8] = 1.0
+    A = W.from_dense(D)
+    r = O.gmres(A, np.ones(8), m=5, fmt=O.F64, precond=O.PC_BJ4, tol=1e-10)
+    assert r["status"] == O.ERR_ARG
+
+
+def test_block_jacobi_reduces_iterations_on_poisson():
+    """Block-Jacobi with 4-row blocks contains the x-direction couplings of a 2D Poisson
+    grid, so it needs fewer iterations than point Jacobi (which on a constant diagonal
+    is no preconditioning at all)."""
+    A = W.poisson2d(16, 16)
+    b = np.random.default_rng(4).standard_normal(A.n)
+    rj = O.gmres(A, b, m=30, fmt=O.F64, precond=O.PC_JACOBI, tol=1e-10)
+    rb = O.gmres(A, b, m=30, fmt=O.F64, precond=O.PC_BJ4, tol=1e-10)
+    assert rj["status"] == rb["status"] == O.OK
+    assert rb["iters"] < rj["iters"]
