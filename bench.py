@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--formats", default="f64,f32,f16,i32,i16")
     p.add_argument("--headline", default="f32")
     p.add_argument("--arith", default="df32")
+    p.add_argument("--adapt", action="store_true",
+                   help="adaptive basis format: promote a format up its ladder when a cycle loses accuracy")
     p.add_argument("--precond", default="none", choices=["none", "jacobi", "bj4"],
                    help="right preconditioner of the conv-diff workload (bj4: block-Jacobi, 4-row blocks)")
     p.add_argument("--tol", type=float, default=1e-10)
@@ -510,7 +512,7 @@ def main():
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, precond=args.precond,
-                                     profile=True)
+                                     adapt=args.adapt, profile=True)
                for f in fmts}
 
     def solve_all(record):
@@ -617,8 +619,10 @@ def main():
             "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "df32" if args.arith == "df32" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.precond == "none" else f"{WORKLOAD}_{args.precond}",
+            "config": {"workload": WORKLOAD + ("" if args.precond == "none" else f"_{args.precond}")
+                                   + ("_adaptive" if args.adapt else ""),
                        "n": n, "nnz": A.nnz, "restart": args.restart, "precond": args.precond,
+                       "adaptive_format": bool(args.adapt),
                        "tol": args.tol, "headline_format": args.headline, "formats": fmts,
                        "arith": ("basis products in double-float (FP32 pairs), SpMV/norms/Givens/"
                                  "least squares in FP64" if args.arith == "df32" else "all FP64"),
@@ -627,6 +631,7 @@ def main():
             "time_to_solution_s": {f: round(t_fmt[f] / 1000, 4) for f in fmts},
             "speedup_vs_f64": {f: round(v, 4) for f, v in speedup.items()},
             "iterations": {f: stats[f]["iters"] for f in fmts},
+            "final_format": {f: stats[f]["fmt_final"] for f in fmts},
             "true_relres": {f: stats[f]["true_relres"] for f in fmts},
             "status": {f: stats[f]["status"] for f in fmts},
             "roofline": roofline,

@@ -103,6 +103,16 @@ typedef struct {
                                 options.stream (read with cbgmres_profile)              */
     int32_t stop_on_stagnation; /* 1: stop with CBG_STAGNATED when the explicit residual
                                    at a restart is not below the previous one (0)      */
+    int32_t adapt;           /* 1: adaptive basis format (no counterpart in the paper, which
+                                fixes one format per solve; Section 5.3 shows the 16-bit
+                                formats losing iterations).  At every restart after the first,
+                                if the explicit residual exceeds adapt_gap times the
+                                recurrence residual the previous cycle ended with, the basis
+                                moves one step up the ladder e4m3 -> bf16 -> f32 -> f64,
+                                f16 -> f32, i16 -> i32 -> f64 for the following cycles.  The
+                                basis is then allocated for 8-byte codes.  Default 0.      */
+    int32_t pad1;
+    double adapt_gap;        /* promotion threshold of adapt (default 4)                */
 } cbg_options;
 
 typedef struct {
@@ -114,11 +124,13 @@ typedef struct {
     double ms_total;         /* wall time of the solve on the stream (CUDA events)     */
     double bytes_model;      /* model HBM bytes: SpMV + 4 basis passes per step         */
     int32_t status;          /* same value as the function's return                    */
-    int32_t pad0;
+    int32_t fmt_final;       /* basis format of the last cycle (differs from the handle's
+                                only with options.adapt)                                */
     double* history;         /* optional host buffer: recurrence residual per step     */
     int64_t history_cap;     /* its capacity (0: none)                                  */
     int64_t history_len;     /* entries written                                         */
     int64_t kernel_launches; /* library kernels launched by this call                   */
+    int64_t promotions;      /* basis format promotions of options.adapt in this solve  */
 } cbg_stats;
 
 /* Per-kernel-class timing gathered while options.profile == 1 (accumulated over

@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 class GmresArgs(C.Structure):
     _fields_ = [
         ("m", C.c_int32), ("fmt", C.c_int32), ("precond", C.c_int32), ("reorth", C.c_int32),
-        ("literal_fig1", C.c_int32), ("pad0", C.c_int32),
+        ("literal_fig1", C.c_int32), ("adapt", C.c_int32),
         ("eta", C.c_double), ("eps_bd", C.c_double), ("tol", C.c_double),
         ("maxit", C.c_int64), ("pvals", C.c_void_p),
         ("H1", C.c_void_p), ("V1", C.c_void_p), ("hist", C.c_void_p), ("hist_cap", C.c_int64),
@@ -61,6 +61,7 @@ class GmresArgs(C.Structure):
         ("nhist", C.c_int64), ("ntres", C.c_int64),
         ("true_relres", C.c_double), ("est_relres", C.c_double),
         ("status", C.c_int32), ("pad1", C.c_int32),
+        ("adapt_gap", C.c_double), ("fmt_final", C.c_int32), ("promotions", C.c_int32),
     ]
 
 
@@ -179,7 +180,7 @@ def gmres(A, b, x0=None, *, m: int = 100, fmt: int = F64, precond: int = PC_NONE
           pvals=None, reorth: int = REORTH_ALWAYS, eta: float = 2 ** -0.5,
           eps_bd: float = 2.0 ** -46, literal_fig1: bool = False, tol: float = 1e-10,
           maxit: int | None = None, want_H1: bool = False, want_V1: bool = False,
-          hist_cap: int = 0, tres_cap: int = 0) -> dict:
+          hist_cap: int = 0, tres_cap: int = 0, adapt: bool = False, adapt_gap: float = 4.0) -> dict:
     """Run the oracle's GMRES(m).  Returns a dict with x, status, iters, cycles, reorths,
     true_relres, est_relres and the optional H1 ((m+1) x m raw Hessenberg of the first
     cycle), V1 (decoded basis of the first cycle), hist, tres."""
@@ -191,6 +192,7 @@ def gmres(A, b, x0=None, *, m: int = 100, fmt: int = F64, precond: int = PC_NONE
     a = GmresArgs()
     a.m, a.fmt, a.precond, a.reorth = m, fmt, precond, reorth
     a.literal_fig1 = int(literal_fig1)
+    a.adapt, a.adapt_gap = int(adapt), adapt_gap
     a.eta, a.eps_bd, a.tol, a.maxit = eta, eps_bd, tol, maxit
     keep = []
     if pvals is not None:
@@ -207,7 +209,8 @@ def gmres(A, b, x0=None, *, m: int = 100, fmt: int = F64, precond: int = PC_NONE
         tres = np.zeros(tres_cap); a.tres = tres.ctypes.data; a.tres_cap = tres_cap
     lib().or_gmres(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), C.byref(a))
     out = dict(x=x, status=a.status, iters=a.iters, cycles=a.cycles, reorths=a.reorths,
-               true_relres=a.true_relres, est_relres=a.est_relres, k1=a.k1)
+               true_relres=a.true_relres, est_relres=a.est_relres, k1=a.k1,
+               fmt_final=a.fmt_final, promotions=a.promotions)
     if H1 is not None:
         out["H1"] = H1.T.copy()            # (m+1) x m
     if V1 is not None:

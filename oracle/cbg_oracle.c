@@ -352,6 +352,17 @@ static int compress_column(int fmt, int64_t n, const double* w, double h, void* 
     return or_decode(fmt, n, codes, scale, vt);
 }
 
+/* Adaptive basis format (reading R15; the paper fixes one format per solve): the next
+ * format up the ladder e4m3 -> bf16 -> f32 -> f64, f16 -> f32, i16 -> i32 -> f64, or -1. */
+static int wider_format(int f)
+{
+    if (f == OR_E4M3) return OR_BF16;
+    if (f == OR_BF16 || f == OR_F16) return OR_F32;
+    if (f == OR_I16) return OR_I32;
+    if (f == OR_F32 || f == OR_I32) return OR_F64;
+    return -1;
+}
+
 /* ===================================================================================
  * GMRES(m), Fig. 1, with the explicit-residual recheck of Section 5.2.
  * =================================================================================== */
@@ -425,6 +436,9 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         goto done;
     }
 
+    int fmt = a->fmt;            /* basis format of the current cycle (adapt moves it up) */
+    double last_est = 0.0;       /* recurrence residual the previous cycle ended with   */
+    a->promotions = 0;
     for (;;) {
         /* Fig. 1 step 1: r0 = b - A x0, beta = ||r0|| */
         or_spmv(n, rowptr, col, val, x, r);
@@ -435,12 +449,21 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         if (a->tres && a->ntres < a->tres_cap) a->tres[a->ntres++] = beta / bnorm;
         if (beta <= target) { a->status = OR_OK; break; }
         if (a->iters >= a->maxit) { a->status = OR_NOT_CONVERGED; break; }
+        /* adapt: the explicit residual exceeds adapt_gap times what the last cycle's
+         * recurrence promised -> the compressed basis limits the solve: widen it */
+        if (a->adapt && a->cycles > 0 && beta > a->adapt_gap * last_est) {
+            const int wf = wider_format(fmt);
+            if (wf >= 0) {
+                fmt = wf;
+                a->promotions++;
+            }
+        }
         a->cycles++;
         int64_t kcap = a->maxit - a->iters;
         if (kcap > m) kcap = m;
 
         /* v = r0 / beta, stored compressed: V_1 = [v] */
-        if (compress_column(a->fmt, n, r, beta, codes, V, tmp)) { a->status = OR_ERR_ARG; break; }
+        if (compress_column(fmt, n, r, beta, codes, V, tmp)) { a->status = OR_ERR_ARG; break; }
         memset(R, 0, (size_t)(m + 1) * (size_t)m * sizeof(double));
         memset(H, 0, (size_t)(m + 1) * (size_t)m * sizeof(double));
         memset(g, 0, ((size_t)m + 1) * sizeof(double));
@@ -500,6 +523,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             double est = fabs(g[j + 1]);
+            last_est = est;
             a->est_relres = est / bnorm;
             if (a->hist && a->nhist < a->hist_cap) a->hist[a->nhist++] = est / bnorm;
             k = j + 1;
@@ -511,7 +535,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             /* recurrence residual signals convergence (Section 5.2) */
             if (est <= target) break;
             /* steps 13-14: v = w / h_{j+1,j}, V_{j+1} = [V_j, v] (stored compressed) */
-            if (compress_column(a->fmt, n, w, hn, codes, V + (size_t)(j + 1) * (size_t)n, tmp)) {
+            if (compress_column(fmt, n, w, hn, codes, V + (size_t)(j + 1) * (size_t)n, tmp)) {
                 nonfinite = 1;
                 break;
             }
@@ -541,6 +565,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         /* step 18: go to step 1 (the explicit residual decides) */
     }
 done:
+    a->fmt_final = fmt;
     free(V); free(codes); free(r); free(w); free(z); free(tmp); free(H); free(R);
     free(cs); free(sn); free(g); free(h); free(u); free(y); free(diag); free(binv);
     return a->status;

@@ -95,7 +95,7 @@ typedef struct {
     int32_t precond;        /* OR_PC_*                                              */
     int32_t reorth;         /* OR_REORTH_*                                          */
     int32_t literal_fig1;   /* 1: Fig. 1 step 12 taken literally (reading R2)      */
-    int32_t pad0;
+    int32_t adapt;          /* 1: adaptive basis format (reading R15)              */
     double  eta;            /* conditional re-orthogonalisation threshold          */
     double  eps_bd;         /* breakdown threshold on h_{j+1,j} / omega            */
     double  tol;            /* tau                                                  */
@@ -112,6 +112,9 @@ typedef struct {
     int64_t iters, cycles, reorths, k1, nhist, ntres;
     double  true_relres, est_relres;
     int32_t status, pad1;
+    double  adapt_gap;      /* promotion threshold of adapt                         */
+    int32_t fmt_final;      /* out: basis format of the last cycle                  */
+    int32_t promotions;     /* out: format promotions                               */
 } or_gmres_args;
 
 int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,

@@ -21,6 +21,7 @@ from .build import LIB as _LIB_PATH
 from .build import build as _build
 
 FORMATS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "i32": 5, "i16": 6}
+FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
 FORMAT_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i16": 2}
 PRECONDS = {"none": 0, "jacobi": 1, "spai": 2, "bj4": 3}
 REORTH = {"always": 0, "conditional": 1, "never": 2}
@@ -48,15 +49,16 @@ class Options(C.Structure):
     _fields_ = [("reorth", C.c_int32), ("precond", C.c_int32), ("arith", C.c_int32),
                 ("spmv_group", C.c_int32), ("eta", C.c_double), ("breakdown_eps", C.c_double),
                 ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32),
-                ("profile", C.c_int32), ("stop_on_stagnation", C.c_int32)]
+                ("profile", C.c_int32), ("stop_on_stagnation", C.c_int32), ("adapt", C.c_int32),
+                ("pad1", C.c_int32), ("adapt_gap", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("reorths", C.c_int64),
                 ("true_relres", C.c_double), ("est_relres", C.c_double), ("ms_total", C.c_double),
-                ("bytes_model", C.c_double), ("status", C.c_int32), ("pad0", C.c_int32),
+                ("bytes_model", C.c_double), ("status", C.c_int32), ("fmt_final", C.c_int32),
                 ("history", C.c_void_p), ("history_cap", C.c_int64), ("history_len", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("promotions", C.c_int64)]
 
 
 class Profile(C.Structure):
@@ -160,7 +162,7 @@ def _dev_f64(t, n=None, name="vector"):
 
 def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=None,
             check_every=4, eta=None, breakdown_eps=None, profile=False,
-            stop_on_stagnation=False) -> Options:
+            stop_on_stagnation=False, adapt=False, adapt_gap=None) -> Options:
     o = Options()
     lib().cbgmres_options_default(C.byref(o))
     o.precond = PRECONDS[precond]
@@ -170,6 +172,9 @@ def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=
     o.check_every = check_every
     o.profile = int(bool(profile))
     o.stop_on_stagnation = int(bool(stop_on_stagnation))
+    o.adapt = int(bool(adapt))
+    if adapt_gap is not None:
+        o.adapt_gap = adapt_gap
     if eta is not None:
         o.eta = eta
     if breakdown_eps is not None:
@@ -180,7 +185,8 @@ def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=
 
 def _stats_dict(st: Stats, hist=None) -> dict:
     out = {k: getattr(st, k) for k in ("iters", "restarts", "reorths", "true_relres", "est_relres",
-                                       "ms_total", "bytes_model", "status", "kernel_launches")}
+                                       "ms_total", "bytes_model", "status", "kernel_launches", "promotions")}
+    out["fmt_final"] = FORMAT_NAMES.get(st.fmt_final, st.fmt_final)
     if hist is not None:
         out["history"] = hist[: st.history_len].copy()
     return out
@@ -195,7 +201,7 @@ class Solver:
     def __init__(self, rowptr, col, val, *, restart: int = 100, fmt: str = "f64",
                  precond: str = "none", arith: str = "df32", reorth: str = "always",
                  spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False,
-                 stop_on_stagnation: bool = False):
+                 stop_on_stagnation: bool = False, adapt: bool = False, adapt_gap: float | None = None):
         torch = _torch()
         L = lib()
         self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
@@ -213,7 +219,7 @@ class Solver:
         self.ld = (self.n + TILE_ROWS - 1) // TILE_ROWS * TILE_ROWS
         opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
                       stream=stream, check_every=check_every, profile=profile,
-                      stop_on_stagnation=stop_on_stagnation)
+                      stop_on_stagnation=stop_on_stagnation, adapt=adapt, adapt_gap=adapt_gap)
         h = C.c_void_p()
         _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
                "cbgmres_create")

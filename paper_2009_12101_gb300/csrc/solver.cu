@@ -96,6 +96,21 @@ const Ops& ops_for(int fmt)
 
 long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
 
+// Next basis format of the adaptive ladder (options.adapt): e4m3 -> bf16 -> f32 -> f64,
+// f16 -> f32, i16 -> i32 -> f64; -1 at the top.
+int promote_format(int fmt)
+{
+    switch (fmt) {
+    case CBG_E4M3: return CBG_BF16;
+    case CBG_BF16: return CBG_F32;
+    case CBG_F16: return CBG_F32;
+    case CBG_I16: return CBG_I32;
+    case CBG_F32: return CBG_F64;
+    case CBG_I32: return CBG_F64;
+    default: return -1;
+    }
+}
+
 // --------------------------------------------------------------- small helper kernels
 // w as double-float hi and lo planes, for the dot kernels
 __global__ void k_split_df(const double* w, long long n, float* out)
@@ -345,6 +360,7 @@ struct cbg_handle {
     long long hist_alloc = 0;
     int grid_dot = 0, grid_axpy = 0, grid_store = 0, grid_spmv = 0, group = 1, gridmax = 0;
     int grid_tma = 0;         // bulk-copy pipelined basis kernels: one block per SM
+    int fmt0 = 0;             // the handle's basis format (options.adapt may move up from it)
     bool use_tma = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> step_ev;
@@ -448,6 +464,18 @@ double spmv_bytes(const cbg_handle* h)
 double store_bytes(const cbg_handle* h) { return (double)h->n * (8.0 + (double)fmt_bytes(h->fmt)); }
 
 // ------------------------------------------------------------------ launches per step
+// Basis format of the following cycles: code stride and the format-dependent grids.
+void set_format(cbg_handle* h, int fmt)
+{
+    const Ops& op = ops_for(fmt);
+    const int sms = num_sms();
+    h->fmt = fmt;
+    h->ldb = h->ld * fmt_bytes(fmt);
+    h->grid_dot = std::max(1, (int)std::min<long long>(h->ld / DOT_MIN_ROWS, (long long)sms * std::max(1, op.occ_dot())));
+    const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
+    h->grid_axpy = std::max(1, (int)std::min<long long>(axpy_blocks, (long long)sms * std::max(1, op.occ_axpy())));
+}
+
 SpmvArgs spmv_args(cbg_handle* h)
 {
     SpmvArgs a{};
@@ -645,6 +673,8 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
 {
     if (!h || !b || !x || !(tol >= 0.0) || maxit < 0) return CBG_ERR_ARG;
     cudaStream_t s = h->stream;
+    if (h->fmt != h->fmt0) set_format(h, h->fmt0);   // every solve starts in the handle's format
+    long long promotions = 0;
     CBG_CUDA(cudaEventRecord(h->ev0, s));
     // ||b|| and finiteness of b and x0
     const long long launches0 = h->launches;
@@ -702,6 +732,15 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
                 stagnated = true;
                 break;
             }
+            // adaptive basis format: the compressed basis lost more accuracy in the last
+            // cycle than its recurrence residual accounts for -> next format of the ladder
+            if (h->opt.adapt && cycles > 0 && hs.beta > h->opt.adapt_gap * hs.est) {
+                const int nf = promote_format(h->fmt);
+                if (nf >= 0) {
+                    set_format(h, nf);
+                    promotions++;
+                }
+            }
             prev_beta = hs.beta;
             iters_before = hs.iters;
             cycles++;
@@ -739,6 +778,8 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
         stats->ms_total = ms;
         stats->bytes_model = bytes;
         stats->status = status;
+        stats->fmt_final = h->fmt;
+        stats->promotions = promotions;
         stats->history_len = 0;
         if (hist_cap > 0 && bnorm > 0) {
             long long nh = std::min<long long>(hs.iters, hist_cap);
@@ -770,6 +811,8 @@ void cbgmres_options_default(cbg_options* o)
     o->use_graph = 0;
     o->profile = 0;
     o->stop_on_stagnation = 0;
+    o->adapt = 0;
+    o->adapt_gap = 4.0;
 }
 
 const char* cbgmres_status_string(int s)
@@ -883,35 +926,35 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
         if (hbad) TRY(CBG_ERR_ARG);
     }
-    TRY(dalloc(&h->V, (size_t)(restart + 1) * h->ldb));
-    if (cudaMemset(h->V, 0, (size_t)(restart + 1) * h->ldb) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    // the adaptive ladder may end at f64: room for 8-byte codes
+    const size_t vbytes = (size_t)(restart + 1) * h->ld * (o.adapt ? 8 : fmt_bytes(fmt));
+    TRY(dalloc(&h->V, vbytes));
+    if (cudaMemset(h->V, 0, vbytes) != cudaSuccess) TRY(CBG_ERR_CUDA);
     double** vecs[] = {&h->w, &h->w1, &h->w2, &h->r, &h->tmp, &h->z, &h->wdf};
     for (double** p : vecs) {
         TRY(dalloc(p, h->ld));
         if (cudaMemset(*p, 0, h->ld * sizeof(double)) != cudaSuccess) TRY(CBG_ERR_CUDA);
     }
 
-    // launch geometry
-    const Ops& op = ops_for(fmt);
+    // launch geometry (format-dependent parts: set_format; with options.adapt the
+    // per-block partial arrays are sized for every format of the ladder)
     const int sms = num_sms();
-    const int occ_dot = std::max(1, op.occ_dot());
-    const int occ_axpy = std::max(1, op.occ_axpy());
     const int occ_spmv = std::max(1, spmv_occupancy());
-    h->grid_dot = (int)std::min<long long>(h->ld / DOT_MIN_ROWS, (long long)sms * occ_dot);
-    const long long axpy_blocks = h->ld / ((long long)THREADS * (16 / fmt_bytes(fmt)));
-    h->grid_axpy = (int)std::min<long long>(axpy_blocks, (long long)sms * occ_axpy);
+    h->fmt0 = fmt;
     h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
     h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
     h->grid_spmv = (int)std::min<long long>((n * h->group + THREADS - 1) / THREADS, (long long)sms * occ_spmv);
-    h->grid_dot = std::max(1, h->grid_dot);
-    h->grid_axpy = std::max(1, h->grid_axpy);
     h->grid_store = std::max(1, h->grid_store);
     h->grid_spmv = std::max(1, h->grid_spmv);
     h->grid_tma = sms;
     h->use_tma = o.arith == CBG_ARITH_DF32;
-    if (o.arith == CBG_ARITH_DF32 && !op.tma_fits()) TRY(CBG_ERR_UNSUPPORTED);
-    h->gridmax = std::max(std::max(std::max(h->grid_dot, h->grid_axpy), std::max(h->grid_store, h->grid_spmv)),
-                          h->grid_tma);
+    h->gridmax = std::max(std::max(h->grid_store, h->grid_spmv), h->grid_tma);
+    for (int f = fmt; f >= 0; f = o.adapt ? promote_format(f) : -1) {
+        if (o.arith == CBG_ARITH_DF32 && !ops_for(f).tma_fits()) TRY(CBG_ERR_UNSUPPORTED);
+        set_format(h, f);
+        h->gridmax = std::max(h->gridmax, std::max(h->grid_dot, h->grid_axpy));
+    }
+    set_format(h, fmt);
 
     // state block: DevState + H, R, cs, sn, g, y, h, u, scales + partials + counters
     const int m = restart, ldh = m + 1;

@@ -124,6 +124,30 @@ def test_block_jacobi_rejects_singular_block():
     assert e.value.status == -1
 
 
+@pytest.mark.parametrize("fmt", ["e4m3", "bf16", "i16", "f32"])
+def test_adaptive_format_parity(fmt):
+    """options.adapt: the GPU takes the same promotions as the oracle's independent
+    implementation of the policy, and then agrees on iterations and x."""
+    torch, cb = need_gpu()
+    A = W.convdiff3d(16)
+    xs = W.exact_solution(A.n, 2); b = W.rhs_from_solution(A, xs)
+    ro = O.gmres(A, b, m=30, fmt=O.FORMATS[fmt], tol=1e-10, adapt=True, maxit=5000)
+    assert ro["status"] == O.OK
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=30, fmt=fmt, adapt=True) as s:
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000)
+        assert st["status"] == 0
+        assert st["promotions"] == ro["promotions"]
+        assert st["fmt_final"] == cb.FORMAT_NAMES[ro["fmt_final"]]
+        assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+        x = xg.cpu().numpy()
+        assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+        # a second solve starts again in the handle's format
+        xg.zero_()
+        st2 = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=5000)
+        assert st2["promotions"] == st["promotions"] and st2["iters"] == st["iters"]
+
+
 def test_spai_equal_to_jacobi_when_p_is_diagonal():
     """P = D^{-1} on A's pattern (zeros off the diagonal) is the Jacobi preconditioner."""
     torch, cb = need_gpu()

@@ -357,3 +357,42 @@ def test_block_jacobi_reduces_iterations_on_poisson():
     rb = O.gmres(A, b, m=30, fmt=O.F64, precond=O.PC_BJ4, tol=1e-10)
     assert rj["status"] == rb["status"] == O.OK
     assert rb["iters"] < rj["iters"]
+
+
+# -------------------------------------------------- adaptive basis format (reading R15)
+def _cd16():
+    A = W.convdiff3d(16)
+    xs = W.exact_solution(A.n, 2)
+    return A, W.rhs_from_solution(A, xs)
+
+
+def test_adapt_never_moves_f64_and_huge_gap_is_static():
+    A, b = _cd16()
+    for fmt, gap in ((O.F64, 4.0), (O.E4M3, 1e300), (O.F16, 1e300)):
+        r0 = O.gmres(A, b, m=30, fmt=fmt, tol=1e-10)
+        r1 = O.gmres(A, b, m=30, fmt=fmt, tol=1e-10, adapt=True, adapt_gap=gap)
+        assert r1["promotions"] == 0 and r1["fmt_final"] == fmt
+        assert r1["iters"] == r0["iters"] and np.array_equal(r1["x"], r0["x"])
+
+
+def test_adapt_zero_gap_climbs_the_whole_ladder():
+    """gap 0 promotes at every restart: e4m3 -> bf16 -> f32 -> f64, then stays."""
+    A, b = _cd16()
+    r = O.gmres(A, b, m=8, fmt=O.E4M3, tol=1e-10, adapt=True, adapt_gap=0.0)
+    assert r["status"] == O.OK and r["cycles"] >= 4
+    assert r["promotions"] == 3 and r["fmt_final"] == O.F64
+    r = O.gmres(A, b, m=8, fmt=O.I16, tol=1e-10, adapt=True, adapt_gap=0.0)
+    assert r["promotions"] == 2 and r["fmt_final"] == O.F64
+
+
+def test_adapt_rescues_an_8_bit_basis():
+    """The e4m3 basis loses many iterations on conv-diff 16^3; the adaptive solve
+    promotes it and needs far fewer, while reaching the same true residual."""
+    A, b = _cd16()
+    r0 = O.gmres(A, b, m=30, fmt=O.E4M3, tol=1e-10)
+    r1 = O.gmres(A, b, m=30, fmt=O.E4M3, tol=1e-10, adapt=True)
+    rf = O.gmres(A, b, m=30, fmt=O.F64, tol=1e-10)
+    assert r0["status"] == r1["status"] == O.OK
+    assert r1["promotions"] >= 1 and r1["iters"] < 0.8 * r0["iters"]
+    assert r1["iters"] >= rf["iters"]
+    assert r1["true_relres"] <= 1e-10
