@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
-    p.add_argument("--workload", choices=["convdiff128", "batch512", "random27", "learned96", "restart_sweep"],
+    p.add_argument("--workload", choices=["convdiff128", "batch512", "random27", "learned96", "restart_sweep",
+                                          "multirhs"],
                    default="convdiff128")
     return p.parse_args()
 
@@ -472,6 +473,53 @@ def run_restart_sweep(args):
     return 0
 
 
+# ------------------------------------------------------------------------ multi-RHS basis product
+def run_multirhs(args):
+    """H = V^T W for k = 8 vectors sharing one f32 basis (n = 2^21, 100 columns): one
+    multi-RHS launch against 8 single-vector launches of the same kernel."""
+    import torch
+    import paper_2009_12101_gb300 as cb
+    cb.ensure_built()
+    n, ncols, k = 1 << 21, 100, 8
+    ld = n
+    rng = np.random.default_rng(20201207)
+    stream = torch.cuda.current_stream()
+    V = torch.from_numpy(rng.standard_normal((ncols, ld)).astype(np.float32) / np.sqrt(n)).cuda()
+    Vb = V.view(torch.uint8)
+    scales = np.ones(ncols)
+    W = torch.from_numpy(rng.standard_normal((k, n))).cuda()
+    ws = torch.empty(cb.lib().cbg_basis_dot_multi_workspace(ld, ncols, k), dtype=torch.uint8, device="cuda")
+    def one():
+        return cb.basis_dot_multi("f32", n, Vb, ld, scales, W, workspace=ws)
+    def each():
+        for r in range(k):
+            cb.basis_dot_multi("f32", n, Vb, ld, scales, W[r:r + 1], workspace=ws)
+    out = {}
+    for name, fn in (("k8", one), ("8x_k1", each)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / args.steps
+    vbytes = ncols * n * 4
+    line = {"metric": METRIC, "value": round(out["8x_k1"] / out["k8"], 4), "unit": "x", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(out["k8"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+            "config": {"workload": "multirhs_f32_n2097152_cols100_k8",
+                       "value_is": "time(8 launches with k = 1) / time(1 launch with k = 8)"},
+            "ms": {kk: round(v, 4) for kk, v in out.items()},
+            "basis_gbs_k8": round(vbytes / (out["k8"] * 1e-3) / 1e9, 1),
+            "df_mac_per_s_k8": round(ncols * n * k / (out["k8"] * 1e-3), 1),
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -485,6 +533,8 @@ def main():
         return run_learned96(args)
     if args.workload == "restart_sweep":
         return run_restart_sweep(args)
+    if args.workload == "multirhs":
+        return run_multirhs(args)
     import torch
     import torch.distributed as dist
 

@@ -220,6 +220,24 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
 int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
                    const double* scales, const double* h, double* w, void* stream);
 
+/* ---- multi-RHS basis product: H = V^T W for k <= 8 vectors sharing one basis -------
+ * No counterpart in the paper (its GMRES has one right-hand side); the building block of
+ * block Krylov orthogonalisation.  Reads V once for all k vectors (one split-K product
+ * in double-float arithmetic, like cbg_basis_dot with arith = CBG_ARITH_DF32).
+ *   V: device codes of format fmt, ncols (<= 256) columns of leading dimension ld
+ *      elements (ld >= n, ld % 4096 == 0, rows n..ld-1 zero);
+ *   scales[ncols]: device decode factors;  W: device, n x k column-major, leading
+ *      dimension ldw >= n (only rows < n are read);
+ *   H: device, ncols x k row-major: H[c*k + r] = sum_i dec(V[i,c]) W[i,r];
+ *   workspace: device scratch of at least cbg_basis_dot_multi_workspace(ld, ncols, k)
+ *      bytes, owned by the caller, not shared between concurrent calls.
+ * Asynchronous on `stream` (no allocation, no synchronisation).  Errors: CBG_ERR_ARG
+ * (sizes, null pointers, workspace too small), CBG_ERR_CUDA. */
+size_t cbg_basis_dot_multi_workspace(int64_t ld, int ncols, int k);
+int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
+                        const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
+                        void* stream);
+
 /* Copy the accumulated per-kernel profile of a handle (options.profile == 1) into
  * *out; reset != 0 clears it afterwards.  Errors: CBG_ERR_ARG. */
 int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset);

@@ -109,6 +109,9 @@ def lib():
             L.cbg_basis_dot.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
             L.cbg_basis_axpy.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
             L.cbg_basis_dot_noalloc.argtypes = [i32, i32, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.cbg_basis_dot_multi_workspace.argtypes = [i64, i32, i32]
+            L.cbg_basis_dot_multi_workspace.restype = C.c_size_t
+            L.cbg_basis_dot_multi.argtypes = [i32, i64, i32, vp, i64, vp, i32, vp, i64, vp, vp, C.c_size_t, vp]
             L.cbgmres_create_batched.argtypes = [i32, vp, i32, i32, C.POINTER(Options), C.POINTER(vp)]
             L.cbgmres_solve_batched.argtypes = [vp, vp, vp, d, i64, vp]
             L.cbgmres_tune_batched.argtypes = [vp, vp, vp, d, i64, C.c_char_p, C.POINTER(C.c_int),
@@ -350,6 +353,27 @@ def basis_dot_noalloc(fmt: str, arith: str, n: int, V, ld: int, scales, w, strea
                                        C.c_void_p(sc.ctypes.data), _dev_f64(w), C.c_void_p(h.ctypes.data),
                                        _stream_ptr(stream)), "cbg_basis_dot_noalloc")
     return h
+
+
+def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None):
+    """H = V^T W for k <= 8 vectors (W: CUDA float64 tensor n x k, or k x ld rows as
+    columns, see below); V: code matrix (ncols x ld codes).  Returns H as a CUDA tensor
+    (ncols x k).  W is given as a (k, ldw) tensor whose row r holds vector r."""
+    torch = _torch()
+    ncols = V.shape[0]
+    k, ldw = int(W.shape[0]), int(W.shape[1])
+    sc = torch.as_tensor(np.ascontiguousarray(scales, np.float64)).cuda()
+    H = torch.empty(ncols, k, dtype=torch.float64, device=W.device)
+    ws_bytes = lib().cbg_basis_dot_multi_workspace(ld, ncols, k)
+    if ws_bytes == 0:
+        raise CbgError(-1, "cbg_basis_dot_multi_workspace")
+    if workspace is None or workspace.numel() < ws_bytes:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=W.device)
+    _check(lib().cbg_basis_dot_multi(FORMATS[fmt], n, ncols, C.c_void_p(V.data_ptr()), ld,
+                                     C.c_void_p(sc.data_ptr()), k, C.c_void_p(W.data_ptr()), ldw,
+                                     C.c_void_p(H.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                     workspace.numel(), _stream_ptr(stream)), "cbg_basis_dot_multi")
+    return H
 
 
 def basis_axpy(fmt: str, arith: str, n: int, V, ld: int, scales, h, w, stream=None):

@@ -164,15 +164,18 @@ __device__ __forceinline__ void d_fold_level(double* D, int lane, int o)
     }
 }
 
-// Fold CG per-lane sums (CG = 4, 8 or 16) into per-column warp sums.  Returns the column
-// (0..CG-1) whose total this lane holds; lanes whose bits below the transposing levels
-// (lane & fold_low<CG>()) are zero hold distinct columns (the others hold copies).
-template <int CG> __host__ __device__ constexpr int fold_low() { return CG == 16 ? 1 : (CG == 8 ? 3 : 7); }
+// Fold CG per-lane sums (CG = 4, 8, 16 or 32) into per-column warp sums.  Returns the
+// column (0..CG-1) whose total this lane holds; lanes whose bits below the transposing
+// levels (lane & fold_low<CG>()) are zero hold distinct columns (the others hold copies).
+template <int CG> __host__ __device__ constexpr int fold_low()
+{
+    return CG == 32 ? 0 : (CG == 16 ? 1 : (CG == 8 ? 3 : 7));
+}
 
 template <int CG>
 __device__ __forceinline__ int df_warp_fold(float* S, float* C, int lane)
 {
-    static_assert(CG == 4 || CG == 8 || CG == 16, "fold width");
+    static_assert(CG == 4 || CG == 8 || CG == 16 || CG == 32, "fold width");
     int col = 0;
     df_fold_level<CG>(S, C, lane, 16);
     col += ((lane >> 4) & 1) * (CG / 2);
@@ -182,9 +185,13 @@ __device__ __forceinline__ int df_warp_fold(float* S, float* C, int lane)
         df_fold_level<CG / 4>(S, C, lane, 4);
         col += ((lane >> 2) & 1) * (CG / 8);
     }
-    if constexpr (CG == 16) {
-        df_fold_level<2>(S, C, lane, 2);
-        col += (lane >> 1) & 1;
+    if constexpr (CG >= 16) {
+        df_fold_level<CG / 8>(S, C, lane, 2);
+        col += ((lane >> 1) & 1) * (CG / 16);
+    }
+    if constexpr (CG == 32) {
+        df_fold_level<2>(S, C, lane, 1);
+        col += lane & 1;
     }
     // the remaining levels are plain butterflies over the one value left
 #pragma unroll

@@ -1,0 +1,50 @@
+"""Multi-RHS basis product H = V^T W (k <= 8 vectors sharing one compressed basis)
+against the oracle's dot products, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import FORMATS, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _basis(fmt, n, ncols, ld, seed):
+    rng = np.random.default_rng(seed)
+    f = O.FORMATS[fmt]
+    itemsize = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i16": 2}[fmt]
+    codes = np.zeros((ncols, ld * itemsize), dtype=np.uint8)
+    scales = np.zeros(ncols)
+    dec = np.zeros((ncols, n))
+    for c in range(ncols):
+        w = rng.standard_normal(n) * np.exp(rng.uniform(-4, 2, n))
+        cd, s, d = O.compress_roundtrip(f, w, np.linalg.norm(w))
+        codes[c, : n * itemsize] = cd.view(np.uint8)
+        scales[c] = s
+        dec[c] = d
+    return codes, scales, dec
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("n,ncols,k", [(5000, 1, 1), (12289, 13, 3), (40000, 40, 8), (70001, 9, 5), (9000, 101, 4)])
+def test_basis_dot_multi_matches_oracle(fmt, n, ncols, k):
+    torch, cb = need_gpu()
+    ld = (n + 4095) // 4096 * 4096
+    codes, scales, dec = _basis(fmt, n, ncols, ld, seed=n + ncols + k)
+    rng = np.random.default_rng(k)
+    W = rng.standard_normal((k, n)) * np.exp(rng.uniform(-3, 3, (k, 1)))
+    Vt = torch.from_numpy(codes).cuda()
+    Wd = torch.from_numpy(W).cuda()
+    H = cb.basis_dot_multi(fmt, n, Vt, ld, scales, Wd).cpu().numpy()
+    ref = np.array([[O.dot(dec[c], W[r]) for r in range(k)] for c in range(ncols)])
+    tol = 1e-13 * np.linalg.norm(dec, axis=1)[:, None] * np.linalg.norm(W, axis=1)[None, :]
+    assert H.shape == (ncols, k)
+    assert np.all(np.abs(H - ref) <= tol), np.max(np.abs(H - ref) / tol)
+
+
+def test_basis_dot_multi_rejects_bad_arguments():
+    torch, cb = need_gpu()
+    V = torch.zeros((3, 4096 * 4), dtype=torch.uint8, device="cuda")
+    W = torch.zeros((9, 4096), dtype=torch.float64, device="cuda")
+    with pytest.raises(cb.CbgError):
+        cb.basis_dot_multi("f32", 4096, V, 4096, np.ones(3), W)     # k = 9 > 8
