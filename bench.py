@@ -475,8 +475,9 @@ def run_restart_sweep(args):
 
 # ------------------------------------------------------------------------ multi-RHS basis product
 def run_multirhs(args):
-    """H = V^T W for k = 8 vectors sharing one f32 basis (n = 2^21, 100 columns): one
-    multi-RHS launch against 8 single-vector launches of the same kernel."""
+    """H = V^T W for k = 8 vectors sharing one basis (n = 2^21, 100 columns): the f16 basis
+    on the tensor cores (tcgen05, exact digit products) and on the CUDA cores (double-float),
+    the f32 basis on the CUDA cores, and 8 single-vector launches for comparison."""
     import torch
     import paper_2009_12101_gb300 as cb
     cb.ensure_built()
@@ -484,18 +485,21 @@ def run_multirhs(args):
     ld = n
     rng = np.random.default_rng(20201207)
     stream = torch.cuda.current_stream()
-    V = torch.from_numpy(rng.standard_normal((ncols, ld)).astype(np.float32) / np.sqrt(n)).cuda()
-    Vb = V.view(torch.uint8)
+    v32 = rng.standard_normal((ncols, ld)) / np.sqrt(n)
+    V32 = torch.from_numpy(v32.astype(np.float32)).cuda().view(torch.uint8)
+    V16 = torch.from_numpy(v32.astype(np.float16)).cuda().view(torch.uint8)
     scales = np.ones(ncols)
     W = torch.from_numpy(rng.standard_normal((k, n))).cuda()
     ws = torch.empty(cb.lib().cbg_basis_dot_multi_workspace(ld, ncols, k), dtype=torch.uint8, device="cuda")
-    def one():
-        return cb.basis_dot_multi("f32", n, Vb, ld, scales, W, workspace=ws)
-    def each():
-        for r in range(k):
-            cb.basis_dot_multi("f32", n, Vb, ld, scales, W[r:r + 1], workspace=ws)
+    cases = {
+        "f16_tensor_k8": lambda: cb.basis_dot_multi("f16", n, V16, ld, scales, W, workspace=ws, path="tensor"),
+        "f16_cuda_k8": lambda: cb.basis_dot_multi("f16", n, V16, ld, scales, W, workspace=ws, path="cuda"),
+        "f32_cuda_k8": lambda: cb.basis_dot_multi("f32", n, V32, ld, scales, W, workspace=ws, path="cuda"),
+        "f16_tensor_8x_k1": lambda: [cb.basis_dot_multi("f16", n, V16, ld, scales, W[r:r + 1], workspace=ws,
+                                                        path="tensor") for r in range(k)],
+    }
     out = {}
-    for name, fn in (("k8", one), ("8x_k1", each)):
+    for name, fn in cases.items():
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -506,16 +510,26 @@ def run_multirhs(args):
         e1.record(stream)
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / args.steps
-    vbytes = ncols * n * 4
-    line = {"metric": METRIC, "value": round(out["8x_k1"] / out["k8"], 4), "unit": "x", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(out["k8"], 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
-            "config": {"workload": "multirhs_f32_n2097152_cols100_k8",
-                       "value_is": "time(8 launches with k = 1) / time(1 launch with k = 8)"},
+    Ht = cases["f16_tensor_k8"]().cpu().numpy()
+    Hc = cases["f16_cuda_k8"]().cpu().numpy()
+    agree = float(np.max(np.abs(Ht - Hc)) / np.max(np.abs(Hc)))
+    peak, kind = measured_peaks()
+    vbytes16 = ncols * n * 2
+    tflops = 3 * 2 * 128 * 128 * n / (out["f16_tensor_k8"] * 1e-3) / 1e12   # 3 digit MMAs, M = N = 128
+    line = {"metric": METRIC, "value": round(out["f16_cuda_k8"] / out["f16_tensor_k8"], 4), "unit": "x",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(out["f16_tensor_k8"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 digits / fp32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": "multirhs_n2097152_cols100_k8",
+                       "value_is": "time(f16 basis, CUDA cores) / time(f16 basis, tensor cores)"},
             "ms": {kk: round(v, 4) for kk, v in out.items()},
-            "basis_gbs_k8": round(vbytes / (out["k8"] * 1e-3) / 1e9, 1),
-            "df_mac_per_s_k8": round(ncols * n * k / (out["k8"] * 1e-3), 1),
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+            "tensor_vs_cuda_max_rel_diff": agree,
+            "roofline": {"bound": "hbm", "kernel": "k_dot_multi_tc (f16 basis, k = 8)",
+                         "achieved": round(vbytes16 / (out["f16_tensor_k8"] * 1e-3) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(vbytes16 / (out["f16_tensor_k8"] * 1e-3) / 1e9 / peak, 4),
+                         "traffic": None, "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)",
+                         "tensor_tflops_issued": round(tflops, 1)},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -237,6 +237,15 @@ size_t cbg_basis_dot_multi_workspace(int64_t ld, int ncols, int k);
 int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
                         const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                         void* stream);
+/* The same product with the implementation chosen by `path`: 0 automatic (what
+ * cbg_basis_dot_multi does), 1 CUDA cores (double-float, every format), 2 tensor cores
+ * (tcgen05, f16 basis with ncols <= 128 and |codes| <= 256, else CBG_ERR_UNSUPPORTED).
+ * The tensor-core path cuts codes and vectors into small integers whose FP16 products
+ * and FP32 sums are exact; W is rounded once, to 56 bits below the largest |W| of each
+ * 2048-row block, so H matches the double-float path to FP64-level accuracy. */
+int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
+                             int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
+                             void* stream, int path);
 
 /* Copy the accumulated per-kernel profile of a handle (options.profile == 1) into
  * *out; reset != 0 clears it afterwards.  Errors: CBG_ERR_ARG. */

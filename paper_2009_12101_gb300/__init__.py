@@ -112,6 +112,8 @@ def lib():
             L.cbg_basis_dot_multi_workspace.argtypes = [i64, i32, i32]
             L.cbg_basis_dot_multi_workspace.restype = C.c_size_t
             L.cbg_basis_dot_multi.argtypes = [i32, i64, i32, vp, i64, vp, i32, vp, i64, vp, vp, C.c_size_t, vp]
+            L.cbg_basis_dot_multi_path.argtypes = [i32, i64, i32, vp, i64, vp, i32, vp, i64, vp, vp, C.c_size_t,
+                                                   vp, i32]
             L.cbgmres_create_batched.argtypes = [i32, vp, i32, i32, C.POINTER(Options), C.POINTER(vp)]
             L.cbgmres_solve_batched.argtypes = [vp, vp, vp, d, i64, vp]
             L.cbgmres_tune_batched.argtypes = [vp, vp, vp, d, i64, C.c_char_p, C.POINTER(C.c_int),
@@ -355,7 +357,7 @@ def basis_dot_noalloc(fmt: str, arith: str, n: int, V, ld: int, scales, w, strea
     return h
 
 
-def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None):
+def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None, path: str = "auto"):
     """H = V^T W for k <= 8 vectors (W: CUDA float64 tensor n x k, or k x ld rows as
     columns, see below); V: code matrix (ncols x ld codes).  Returns H as a CUDA tensor
     (ncols x k).  W is given as a (k, ldw) tensor whose row r holds vector r."""
@@ -369,10 +371,11 @@ def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, worksp
         raise CbgError(-1, "cbg_basis_dot_multi_workspace")
     if workspace is None or workspace.numel() < ws_bytes:
         workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=W.device)
-    _check(lib().cbg_basis_dot_multi(FORMATS[fmt], n, ncols, C.c_void_p(V.data_ptr()), ld,
-                                     C.c_void_p(sc.data_ptr()), k, C.c_void_p(W.data_ptr()), ldw,
-                                     C.c_void_p(H.data_ptr()), C.c_void_p(workspace.data_ptr()),
-                                     workspace.numel(), _stream_ptr(stream)), "cbg_basis_dot_multi")
+    _check(lib().cbg_basis_dot_multi_path(FORMATS[fmt], n, ncols, C.c_void_p(V.data_ptr()), ld,
+                                          C.c_void_p(sc.data_ptr()), k, C.c_void_p(W.data_ptr()), ldw,
+                                          C.c_void_p(H.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                          workspace.numel(), _stream_ptr(stream),
+                                          {"auto": 0, "cuda": 1, "tensor": 2}[path]), "cbg_basis_dot_multi")
     return H
 
 

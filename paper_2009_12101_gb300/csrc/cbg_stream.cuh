@@ -53,14 +53,6 @@ __device__ __forceinline__ void block_tiles(long long ntiles, long long& tb, lon
     te = ((long long)blockIdx.x + 1) * ntiles / gridDim.x;
 }
 
-// every lane waits (acquiring the stage's data for itself); the warp then agrees, so a
-// timeout in one lane never leaves the others at a warp-wide operation
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity)
-{
-    const bool ok = mbar_wait(bar, parity);
-    return __all_sync(0xffffffffu, ok);
-}
-
 __device__ __forceinline__ void record_fault(DevState* st, int* fault)
 {
     if (fault) atomicExch(fault, FAULT_TIMEOUT);

@@ -60,6 +60,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
     return true;
 }
 
+// every lane waits (acquiring the data for itself); the warp then agrees, so a timeout
+// in one lane never leaves the others at a warp-wide operation
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity)
+{
+    const bool ok = mbar_wait(bar, parity);
+    return __all_sync(0xffffffffu, ok);
+}
+
 // L2 policy for data read once (the basis): evict first, so it does not push w out of L2
 __device__ __forceinline__ uint64_t l2_evict_first_policy()
 {

@@ -25,6 +25,9 @@
 using namespace cbg;
 
 void cbg_record_cuda_error(cudaError_t e);   // solver.cu
+size_t cbg_tc_multi_workspace(int64_t ld);   // multi_tc.cu
+int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k, const double* W,
+                 int64_t ldw, double* H, void* workspace, cudaStream_t s, int** fault_out);
 
 namespace {
 
@@ -226,17 +229,26 @@ size_t cbg_basis_dot_multi_workspace(int64_t ld, int ncols, int k)
     const int KR = kr_for(k);
     const size_t split = (size_t)2 * KR * ld * sizeof(float);
     const size_t part = (size_t)multi_grid() * ncols * KR * sizeof(double);
-    return 256 + (split + 255) / 256 * 256 + (part + 255) / 256 * 256;
+    const size_t cuda_core = 256 + (split + 255) / 256 * 256 + (part + 255) / 256 * 256;
+    return std::max(cuda_core, cbg_tc_multi_workspace(ld));
 }
 
-int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
-                        const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes, void* stream)
+int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
+                             const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes, void* stream,
+                             int path)
 {
     if (cbgmres_format_bytes(fmt) == 0 || n < 1 || ncols < 1 || ncols > MAXCOLS || k < 1 || k > KMAX || !V ||
         ld < n || ld % TILE_ROWS || !scales || !W || ldw < n || !H || !workspace ||
-        ws_bytes < cbg_basis_dot_multi_workspace(ld, ncols, k))
+        ws_bytes < cbg_basis_dot_multi_workspace(ld, ncols, k) || path < 0 || path > 2)
         return CBG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool tc_ok = fmt == CBG_F16 && ncols <= 128;
+    if (path == 2 && !tc_ok) return CBG_ERR_UNSUPPORTED;
+    if (path == 2 || (path == 0 && tc_ok)) {
+        int rc = cbg_tc_multi(n, ncols, V, ld, scales, k, W, ldw, H, workspace, s, nullptr);
+        if (rc) { cbg_record_cuda_error(cudaGetLastError()); return rc; }
+        return CBG_OK;
+    }
     const int KR = kr_for(k);
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
@@ -265,6 +277,12 @@ int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld
     e = cudaGetLastError();
     if (e != cudaSuccess) { cbg_record_cuda_error(e); return CBG_ERR_CUDA; }
     return CBG_OK;
+}
+
+int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
+                        const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes, void* stream)
+{
+    return cbg_basis_dot_multi_path(fmt, n, ncols, V, ld, scales, k, W, ldw, H, workspace, ws_bytes, stream, 0);
 }
 
 }  // extern "C"

@@ -48,3 +48,33 @@ def test_basis_dot_multi_rejects_bad_arguments():
     W = torch.zeros((9, 4096), dtype=torch.float64, device="cuda")
     with pytest.raises(cb.CbgError):
         cb.basis_dot_multi("f32", 4096, V, 4096, np.ones(3), W)     # k = 9 > 8
+
+
+@pytest.mark.parametrize("n,ncols,k", [(5000, 1, 1), (12289, 13, 3), (40000, 40, 8), (70001, 9, 5),
+                                        (9000, 101, 4), (20480, 128, 8), (2049, 7, 2)])
+def test_basis_dot_multi_tensor_cores(n, ncols, k):
+    """The tcgen05 path (f16 basis): exact digit products on the tensor cores, compared with
+    the oracle and with the double-float CUDA-core path."""
+    torch, cb = need_gpu()
+    ld = (n + 4095) // 4096 * 4096
+    codes, scales, dec = _basis("f16", n, ncols, ld, seed=3 * n + ncols + k)
+    rng = np.random.default_rng(k + 17)
+    W = rng.standard_normal((k, n)) * np.exp(rng.uniform(-3, 3, (k, 1)))
+    W[:, : n // 3] *= 1e-9                       # blocks of very different magnitude
+    Vt = torch.from_numpy(codes).cuda()
+    Wd = torch.from_numpy(W).cuda()
+    Ht = cb.basis_dot_multi("f16", n, Vt, ld, scales, Wd, path="tensor").cpu().numpy()
+    Hc = cb.basis_dot_multi("f16", n, Vt, ld, scales, Wd, path="cuda").cpu().numpy()
+    ref = np.array([[O.dot(dec[c], W[r]) for r in range(k)] for c in range(ncols)])
+    tol = 1e-13 * np.linalg.norm(dec, axis=1)[:, None] * np.linalg.norm(W, axis=1)[None, :]
+    assert np.all(np.abs(Ht - ref) <= tol), np.max(np.abs(Ht - ref) / tol)
+    assert np.all(np.abs(Ht - Hc) <= 2 * tol)
+
+
+def test_basis_dot_multi_tensor_path_limits():
+    torch, cb = need_gpu()
+    V = torch.zeros((3, 4096 * 4), dtype=torch.uint8, device="cuda")
+    W = torch.zeros((2, 4096), dtype=torch.float64, device="cuda")
+    with pytest.raises(cb.CbgError) as e:
+        cb.basis_dot_multi("f32", 4096, V, 4096, np.ones(3), W, path="tensor")   # f16 only
+    assert e.value.status == -6
