@@ -239,10 +239,12 @@ int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld
                         void* stream);
 /* The same product with the implementation chosen by `path`: 0 automatic (what
  * cbg_basis_dot_multi does), 1 CUDA cores (double-float, every format), 2 tensor cores
- * (tcgen05, f16 basis with ncols <= 128 and |codes| <= 256, else CBG_ERR_UNSUPPORTED).
- * The tensor-core path cuts codes and vectors into small integers whose FP16 products
- * and FP32 sums are exact; W is rounded once, to 56 bits below the largest |W| of each
- * 2048-row block, so H matches the double-float path to FP64-level accuracy. */
+ * (tcgen05, f16 basis with ncols <= 128, else CBG_ERR_UNSUPPORTED).  The tensor-core
+ * path cuts codes and vectors into small pieces whose FP16 products and FP32 sums are
+ * exact; W is truncated once, 54 bits below the largest |W| of each 512-row block, so
+ * H matches the double-float path to FP64-level accuracy.  It covers codes with
+ * |code| <= 1 (the range of normalised basis vectors) and finite W: any other input
+ * makes every entry of H NaN. */
 int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
                              int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                              void* stream, int path);

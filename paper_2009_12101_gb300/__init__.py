@@ -357,15 +357,22 @@ def basis_dot_noalloc(fmt: str, arith: str, n: int, V, ld: int, scales, w, strea
     return h
 
 
-def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None, path: str = "auto"):
-    """H = V^T W for k <= 8 vectors (W: CUDA float64 tensor n x k, or k x ld rows as
-    columns, see below); V: code matrix (ncols x ld codes).  Returns H as a CUDA tensor
-    (ncols x k).  W is given as a (k, ldw) tensor whose row r holds vector r."""
+def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None, path: str = "auto",
+                    out=None):
+    """H = V^T W for k <= 8 vectors; V: code matrix (ncols x ld codes); W: CUDA float64
+    tensor (k, ldw) whose row r holds vector r.  scales: host array or CUDA float64 tensor
+    of the ncols decode factors.  Returns H (CUDA tensor, ncols x k; `out` if given)."""
     torch = _torch()
     ncols = V.shape[0]
     k, ldw = int(W.shape[0]), int(W.shape[1])
-    sc = torch.as_tensor(np.ascontiguousarray(scales, np.float64)).cuda()
-    H = torch.empty(ncols, k, dtype=torch.float64, device=W.device)
+    if torch.is_tensor(scales) and scales.is_cuda and scales.dtype == torch.float64 and scales.is_contiguous():
+        sc = scales
+    else:
+        sc = torch.as_tensor(np.ascontiguousarray(scales, np.float64)).cuda()
+    if out is not None and (out.shape != (ncols, k) or out.dtype != torch.float64 or not out.is_cuda
+                            or not out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA float64 tensor of shape (ncols, k)")
+    H = torch.empty(ncols, k, dtype=torch.float64, device=W.device) if out is None else out
     ws_bytes = lib().cbg_basis_dot_multi_workspace(ld, ncols, k)
     if ws_bytes == 0:
         raise CbgError(-1, "cbg_basis_dot_multi_workspace")

@@ -71,6 +71,65 @@ def test_basis_dot_multi_tensor_cores(n, ncols, k):
     assert np.all(np.abs(Ht - Hc) <= 2 * tol)
 
 
+def _f16_codes(vals, ld):
+    """Raw f16 codes (scale 1) of the columns of vals, zero-padded to ld rows."""
+    ncols, n = vals.shape
+    codes = np.zeros((ncols, ld), dtype=np.float16)
+    codes[:, :n] = vals.astype(np.float16)
+    return codes.view(np.uint8), codes[:, :n].astype(np.float64)
+
+
+def test_basis_dot_multi_tensor_full_code_range():
+    """Codes anywhere in [-1, 1] (subnormals, exact powers of two, the endpoints) are cut
+    exactly; W spans a wide exponent range; many CTAs whose chunk ranges start inside
+    512-row blocks."""
+    torch, cb = need_gpu()
+    n, ncols, k = 400_037, 24, 8
+    ld = (n + 4095) // 4096 * 4096
+    rng = np.random.default_rng(5)
+    vals = rng.uniform(-1, 1, (ncols, n)) * np.exp2(rng.integers(-30, 1, (ncols, n)))
+    vals[:, :8] = [1.0, -1.0, 2.0 ** -24, -(2.0 ** -24), 2.0 ** -14, 0.5, -0.5, 0.99951171875]
+    raw, dec = _f16_codes(vals, ld)
+    W = rng.standard_normal((k, n)) * np.exp2(rng.integers(-40, 40, (k, 1)))
+    W[:, 100_000:200_000] *= np.exp2(rng.integers(-200, 60, (k, 1)))   # blocks far apart in scale
+    Ht = cb.basis_dot_multi("f16", n, torch.from_numpy(raw).cuda(), ld, np.ones(ncols),
+                            torch.from_numpy(W).cuda(), path="tensor").cpu().numpy()
+    ref = np.array([[O.dot(dec[c], W[r]) for r in range(k)] for c in range(ncols)])
+    tol = 1e-13 * np.linalg.norm(dec, axis=1)[:, None] * np.linalg.norm(W, axis=1)[None, :]
+    assert np.all(np.abs(Ht - ref) <= tol), np.max(np.abs(Ht - ref) / tol)
+
+
+@pytest.mark.parametrize("what", ["code_above_1", "w_inf", "w_nan"])
+def test_basis_dot_multi_tensor_flags_inputs_outside_its_range(what):
+    """Inputs the exact digit cut does not cover make the whole result NaN, not a silently
+    wrong number."""
+    torch, cb = need_gpu()
+    n, ncols, k = 10_000, 5, 3
+    ld = 12288
+    rng = np.random.default_rng(6)
+    vals = rng.uniform(-1, 1, (ncols, n))
+    W = rng.standard_normal((k, n))
+    if what == "code_above_1":
+        vals[3, 7777] = 1.5
+    elif what == "w_inf":
+        W[1, 4321] = np.inf
+    else:
+        W[2, 9999] = np.nan
+    raw, _ = _f16_codes(vals, ld)
+    ws = torch.empty(cb.lib().cbg_basis_dot_multi_workspace(ld, ncols, k), dtype=torch.uint8, device="cuda")
+    Ht = cb.basis_dot_multi("f16", n, torch.from_numpy(raw).cuda(), ld, np.ones(ncols),
+                            torch.from_numpy(W).cuda(), workspace=ws, path="tensor").cpu().numpy()
+    assert np.all(np.isnan(Ht))
+    # the next call on the same workspace is clean again
+    W2 = rng.standard_normal((k, n))
+    vals[3, 7777] = 0.5
+    raw, dec = _f16_codes(vals, ld)
+    Ht = cb.basis_dot_multi("f16", n, torch.from_numpy(raw).cuda(), ld, np.ones(ncols),
+                            torch.from_numpy(W2).cuda(), workspace=ws, path="tensor").cpu().numpy()
+    ref = np.array([[O.dot(dec[c], W2[r]) for r in range(k)] for c in range(ncols)])
+    assert np.allclose(Ht, ref, rtol=0, atol=1e-12)
+
+
 def test_basis_dot_multi_tensor_path_limits():
     torch, cb = need_gpu()
     V = torch.zeros((3, 4096 * 4), dtype=torch.uint8, device="cuda")
