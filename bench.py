@@ -690,8 +690,9 @@ def main():
                        "n": n, "nnz": A.nnz, "restart": args.restart, "precond": args.precond,
                        "adaptive_format": bool(args.adapt),
                        "tol": args.tol, "headline_format": args.headline, "formats": fmts,
-                       "arith": ("basis products in double-float (FP32 pairs), SpMV/norms/Givens/"
-                                 "least squares in FP64" if args.arith == "df32" else "all FP64"),
+                       "arith": ("basis products and the per-step SpMV in double-float (FP32 pairs); "
+                                 "residual SpMV, norms, Givens, least squares in FP64"
+                                 if args.arith == "df32" else "all FP64"),
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
                        "l2": "no flush: every basis (>= 0.4 GB per format) exceeds the 129 MB L2"},
             "time_to_solution_s": {f: round(t_fmt[f] / 1000, 4) for f in fmts},

@@ -727,7 +727,32 @@ struct SpmvArgs {
     const int* active;
     float* ydf;               // Arnoldi: also store y split, planar hi[ydf_ld] then lo (may be null)
     long long ydf_ld;
+    // Arnoldi: the values split into FP32 hi[nnz] then lo[nnz] planes; when set, the row
+    // products are formed and summed in double-float instead of FP64 (may be null)
+    const float* valdf;
+    long long nnz;
 };
+
+// One code (or FP64 vector entry) as an FP32 pair with x = xh + xl: exact for every
+// format except FP64 vectors and f64 codes (relative error below 2^-48 there).
+template <int XFMT> __device__ __forceinline__ void xval_df(const void* x, int c, float& xh, float& xl)
+{
+    if constexpr (XFMT < 0 || XFMT == F64) {
+        split_f64(reinterpret_cast<const double*>(x)[c], xh, xl);
+    } else if constexpr (XFMT == I32) {
+        dec_i32(reinterpret_cast<const int*>(x)[c], xh, xl);
+    } else {
+        if constexpr (XFMT == F32) xh = reinterpret_cast<const float*>(x)[c];
+        else if constexpr (XFMT == F16) xh = __half2float(reinterpret_cast<const __half*>(x)[c]);
+        else if constexpr (XFMT == BF16)
+            xh = __uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(x)[c]) << 16);
+        else if constexpr (XFMT == E4M3) {
+            float b;
+            dec_e4m3x2(reinterpret_cast<const unsigned char*>(x)[c], xh, b);
+        } else xh = dec_i16((int)reinterpret_cast<const short*>(x)[c]);
+        xl = 0.f;
+    }
+}
 
 template <int XFMT, int GROUP, int MODE>
 __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
@@ -766,6 +791,16 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
         const unsigned long long ab = (unsigned long long)__double_as_longlong(yv) & 0x7FFFFFFFFFFFFFFFull;
         mxb = ab > mxb ? ab : mxb;
     };
+    // double-float row products (Arnoldi mode, split values): every product val * x is
+    // formed exactly as an FP32 pair (TwoProd) and summed with TwoSum, so the FP64 pipe
+    // only converts the row result; otherwise one FP64 FMA per nonzero
+    const bool dfrows = MODE == SPMV_ARNOLDI && a.valdf != nullptr;
+    constexpr bool XEXACT = XFMT == F32 || XFMT == F16 || XFMT == BF16 || XFMT == E4M3 || XFMT == I16;
+    auto dfadd = [](float& S, float& C, float pr, float er) {   // (S, C) += pr + er
+        const float t = __fadd_rn(S, pr), bb = __fsub_rn(t, S);
+        C = __fadd_rn(C, __fadd_rn(__fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(pr, bb)), er));
+        S = t;
+    };
     for (long long row = gid;; row += ngroups) {
         const bool valid = row < a.n;
         if constexpr (GROUP > 1) {
@@ -775,10 +810,34 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
         }
         const int p0 = valid ? a.rowptr[row] : 0, p1 = valid ? a.rowptr[row + 1] : 0;
         double s = 0.0;
-        for (int p = p0 + lane_g; p < p1; p += GROUP) s = __fma_rn(a.val[p], xval(a.col[p]), s);
-        if constexpr (GROUP > 1) {
+        if (dfrows) {
+            float S = 0.f, C = 0.f;
+            for (int p = p0 + lane_g; p < p1; p += GROUP) {
+                const float vh = a.valdf[p], vl = a.valdf[a.nnz + p];
+                float xh, xl;
+                xval_df<XFMT>(a.x, a.col[p], xh, xl);
+                const float pr = __fmul_rn(vh, xh);
+                float er = __fmaf_rn(vh, xh, -pr);           // exact product error
+                er = __fmaf_rn(vl, xh, er);
+                if constexpr (!XEXACT) er = __fmaf_rn(vh, xl, er);
+                dfadd(S, C, pr, er);
+            }
+            if constexpr (GROUP > 1) {
 #pragma unroll
-            for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+                for (int o = GROUP / 2; o > 0; o >>= 1) {
+                    const float S2 = __shfl_xor_sync(0xFFFFFFFFu, S, o), C2 = __shfl_xor_sync(0xFFFFFFFFu, C, o);
+                    const float t = __fadd_rn(S, S2), bb = __fsub_rn(t, S);
+                    C = __fadd_rn(__fadd_rn(C, C2), __fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(S2, bb)));
+                    S = t;
+                }
+            }
+            s = df_to_double(S, C);
+        } else {
+            for (int p = p0 + lane_g; p < p1; p += GROUP) s = __fma_rn(a.val[p], xval(a.col[p]), s);
+            if constexpr (GROUP > 1) {
+#pragma unroll
+                for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            }
         }
         if (valid && lane_g == 0) finish(row, s);
     }

@@ -112,7 +112,8 @@ int promote_format(int fmt)
 }
 
 // --------------------------------------------------------------- small helper kernels
-// w as double-float hi and lo planes, for the dot kernels
+// a vector as double-float hi and lo planes (w for the dot kernels, the matrix values for
+// the double-float SpMV)
 __global__ void k_split_df(const double* w, long long n, float* out)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -341,6 +342,7 @@ struct cbg_handle {
     int* col = nullptr;
     double* val = nullptr;     // A
     double* valp = nullptr;    // A D^{-1} (Jacobi) or nullptr
+    float* valdf = nullptr;    // the Arnoldi SpMV's values (valp or val) as FP32 hi / lo planes
     double* dinv = nullptr;    // D^{-1}
     double* pvals = nullptr;   // values of P: SPAI (A's pattern) or block-Jacobi inverse blocks
     int* prow = nullptr;       // P's pattern: A's for SPAI, the diagonal blocks for block-Jacobi
@@ -378,7 +380,7 @@ namespace {
 void free_handle(cbg_handle* h)
 {
     if (!h) return;
-    cudaFree(h->rowptr); cudaFree(h->col); cudaFree(h->val); cudaFree(h->valp); cudaFree(h->dinv);
+    cudaFree(h->rowptr); cudaFree(h->col); cudaFree(h->val); cudaFree(h->valp); cudaFree(h->valdf); cudaFree(h->dinv);
     if (h->own_ppat) { cudaFree(h->prow); cudaFree(h->pcol); }
     cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->wdf); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
     cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
@@ -526,6 +528,8 @@ void enqueue_step(cbg_handle* h, int j)
             b2.y = h->w;
             b2.ydf = wdf;
             b2.ydf_ld = h->ld;
+            b2.valdf = wdf ? h->valdf : nullptr;
+            b2.nnz = h->nnz;
             b2.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
         } else {
@@ -533,6 +537,8 @@ void enqueue_step(cbg_handle* h, int j)
             a.y = h->w;
             a.ydf = wdf;
             a.ydf_ld = h->ld;
+            a.valdf = wdf ? h->valdf : nullptr;
+            a.nnz = h->nnz;
             a.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
         }
@@ -910,6 +916,10 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
         if (hbad) TRY(CBG_ERR_ARG);
     }
+    // values of the per-step SpMV split for double-float products
+    TRY(dalloc(&h->valdf, 2 * nnz));
+    k_split_df<<<2048, 256>>>(h->valp ? h->valp : h->val, nnz, h->valdf);
+    if (cudaGetLastError() != cudaSuccess) TRY(CBG_ERR_CUDA);
     h->prow = h->rowptr;
     h->pcol = h->col;
     if (o.precond == CBG_PC_BJ4) {
