@@ -396,6 +396,7 @@ struct AxpyArgs {
     unsigned int* counter;    // EPI_SUB final pass: last block writes st->wnorm, st->wmax
     DevState* st;
     float* wdf_out;           // EPI_SUB: also store w_out split, planar hi[nrows] then lo[nrows] (may be null)
+    const float* wdf_in;      // EPI_SUB, DF32: w_in given as such planes instead (may be null; may equal wdf_out)
 };
 
 // Blocks per SM asked of the register allocator: 4 for 8-byte codes (measured 5 % faster
@@ -485,7 +486,12 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
             if constexpr (ARITH == ARITH_DF32) {
                 if constexpr (EPI == EPI_SUB) {
                     float wh, wl;
-                    split_f64(a.w_in[i], wh, wl);
+                    if (a.wdf_in) {
+                        wh = a.wdf_in[i];
+                        wl = a.wdf_in[a.nrows + i];
+                    } else {
+                        split_f64(a.w_in[i], wh, wl);
+                    }
                     df_add(S[e], C[e], wh, wl);
                 }
                 acc = df_to_double(S[e], C[e]);
@@ -730,7 +736,9 @@ struct SpmvArgs {
     float* ydf;               // Arnoldi: also store y split, planar hi[ydf_ld] then lo (may be null)
     long long ydf_ld;
     // Arnoldi: the values split into FP32 hi[nnz] then lo[nnz] planes; when set, the row
-    // products are formed and summed in double-float instead of FP64 (may be null)
+    // products are formed and summed in double-float instead of FP64, y is delivered only
+    // as its (renormalised) double-float planes ydf (required then) and omega = ||y|| is
+    // summed in double-float (may be null)
     const float* valdf;
     long long nnz;
 };
@@ -803,6 +811,9 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
         C = __fadd_rn(C, __fadd_rn(__fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(pr, bb)), er));
         S = t;
     };
+    float ssS = 0.f, ssC = 0.f, xsh = 1.f, xsl = 0.f;    // double-float rows: ||y||^2, scale
+    const bool xsplit = dfrows && xs != 1.0;
+    if (xsplit) split_f64(xs, xsh, xsl);
     for (long long row = gid;; row += ngroups) {
         const bool valid = row < a.n;
         if constexpr (GROUP > 1) {
@@ -833,7 +844,24 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
                     S = t;
                 }
             }
-            s = df_to_double(S, C);
+            if (valid && lane_g == 0) {
+                float hi, lo;
+                two_sum(S, C, hi, lo);                       // renormalise
+                if (xsplit) {                                // integer / power-of-two scales
+                    const float p = __fmul_rn(hi, xsh);
+                    float e = __fmaf_rn(hi, xsh, -p);
+                    e = __fmaf_rn(hi, xsl, e);
+                    e = __fmaf_rn(lo, xsh, e);
+                    two_sum(p, e, hi, lo);
+                }
+                a.ydf[row] = hi;
+                a.ydf[a.ydf_ld + row] = lo;
+                const float p = __fmul_rn(hi, hi);           // ||y||^2 in double-float
+                float e = __fmaf_rn(hi, hi, -p);
+                e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
+                dfadd(ssS, ssC, p, e);
+            }
+            continue;
         } else {
             for (int p = p0 + lane_g; p < p1; p += GROUP) s = __fma_rn(a.val[p], xval(a.col[p]), s);
             if constexpr (GROUP > 1) {
@@ -846,6 +874,7 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     const double mx = __longlong_as_double((long long)mxb);
     if constexpr (MODE == SPMV_PLAIN || MODE == SPMV_ACCUM) return;
     else {
+        if (dfrows) ss = df_to_double(ssS, ssC);
         ss = warp_sum(ss);
         const double mxw = warp_max(mx);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

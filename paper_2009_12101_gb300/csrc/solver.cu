@@ -578,7 +578,9 @@ void enqueue_step(cbg_handle* h, int j)
     xa.part_norm = h->d.part_norm;
     xa.active = active;
     xa.coef = h->d.h;
-    xa.w_in = h->w;
+    // DF32: the SpMV delivered w only as its double-float planes
+    xa.w_in = wdf ? nullptr : h->w;
+    xa.wdf_in = wdf;
     xa.w_out = reorth ? h->w1 : h->w2;
     xa.st = h->d.st;
     xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
@@ -592,6 +594,7 @@ void enqueue_step(cbg_handle* h, int j)
         launch(h, 0, pass_bytes, run_dot);
         xa.coef = h->d.u;
         xa.w_in = h->w1;
+        xa.wdf_in = nullptr;
         xa.w_out = h->w2;
         xa.wdf_out = nullptr;
         xa.counter = h->d.counters + 5;
