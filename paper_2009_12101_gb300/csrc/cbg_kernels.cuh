@@ -454,17 +454,52 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
             }
         };
         int k = 0;
-        for (; k + U <= ncols; k += U) {
-            uint4 raw[U];
+        if constexpr (ARITH == ARITH_DF32 && BS == 4) {
+            // 4-byte codes (latency-bound): two groups of four columns, software-pipelined,
+            // so the next group's loads are in flight while the current group is
+            // accumulated (measured 3 % faster for f32; slower for the FMA-bound 2-byte codes)
+            constexpr int H = 4;
+            uint4 ra[H], rb[H];
+            if (H <= ncols) {
 #pragma unroll
-            for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
+                for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)q * a.ldb);
+            }
+            for (; k + 2 * H <= ncols; k += 2 * H) {
 #pragma unroll
-            for (int q = 0; q < U; q++) {
-                column(raw[q], cs[k + q]);
-                if constexpr (ARITH == ARITH_DF32) {
-                    if ((q & 3) == 3) {
+                for (int q = 0; q < H; q++) rb[q] = ldg_stream(base + (long long)(k + H + q) * a.ldb);
 #pragma unroll
-                        for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
+#pragma unroll
+                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                if (k + 3 * H <= ncols) {
+#pragma unroll
+                    for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)(k + 2 * H + q) * a.ldb);
+                }
+#pragma unroll
+                for (int q = 0; q < H; q++) column(rb[q], cs[k + H + q]);
+#pragma unroll
+                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+            }
+            if (k + H <= ncols) {             // a last full group of four (already loaded)
+#pragma unroll
+                for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
+#pragma unroll
+                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                k += H;
+            }
+        } else {
+            for (; k + U <= ncols; k += U) {
+                uint4 raw[U];
+#pragma unroll
+                for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
+#pragma unroll
+                for (int q = 0; q < U; q++) {
+                    column(raw[q], cs[k + q]);
+                    if constexpr (ARITH == ARITH_DF32) {
+                        if ((q & 3) == 3) {
+#pragma unroll
+                            for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                        }
                     }
                 }
             }
