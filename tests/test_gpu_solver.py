@@ -61,6 +61,40 @@ def test_full_solve_parity(prob, fmt):
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
+def test_full_size_headline_workload():
+    """The headline workload at full size, in the configuration bench.py times:
+    conv-diff 128^3 (n = 2,097,152), f32 basis, GMRES(100), default options.
+    - The first 10 raw Hessenberg columns against the oracle (10 oracle steps at this
+      size take about a second; they do not depend on the restart length).
+    - The solve's true residual, recomputed by the oracle's SpMV.
+    - The explicit and recurrence residuals agree.
+    - The f64 basis needs the same number of steps within 2 %."""
+    torch, cb = need_gpu()
+    A = W.convdiff3d(128)
+    xs = W.exact_solution(A.n, 2)
+    b = W.rhs_from_solution(A, xs)
+    assert A.n == 2_097_152
+    k, tol = 10, 1e-10
+    ro = O.gmres(A, b, m=k, fmt=O.FORMATS["f32"], tol=0.0, maxit=k, want_H1=True)
+    bd = to_dev(torch, b)
+    iters = {}
+    for fmt in ("f32", "f64"):
+        with cb.Solver.from_csr(A, restart=100, fmt=fmt) as s:
+            if fmt == "f32":
+                Hg = s.arnoldi(bd, torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+                err = col_relerr(Hg, ro["H1"], k)
+                assert np.all(err <= 1e-10), err
+            xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+            st = s.solve(bd, xg, tol=tol, maxit=20000)
+        assert st["status"] == 0, st
+        x = xg.cpu().numpy()
+        r = b - O.spmv(A, x)
+        assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+        assert abs(st["true_relres"] - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-12
+        iters[fmt] = st["iters"]
+    assert abs(iters["f32"] - iters["f64"]) <= max(1, 0.02 * iters["f64"]), iters
+
+
 @pytest.mark.parametrize("arith", ["df32", "fp64"])
 def test_full_solve_fp64_modes_agree(arith):
     torch, cb = need_gpu()
