@@ -124,3 +124,25 @@ def test_learned96_full_size():
         its[pc] = st["iters"]
     assert its["spai"] < its["none"], its
     spai.close()
+
+
+def test_multirhs_full_size():
+    """The multi-RHS product at the size bench.py times (n = 2^21, 100 f16 columns, k = 8),
+    on the tensor cores and on the CUDA cores: 40 sampled entries of H against the
+    oracle's dot, and the two paths against each other everywhere."""
+    torch, cb = need_gpu()
+    n, ncols, k = 1 << 21, 100, 8
+    rng = np.random.default_rng(20201207)
+    v = (rng.standard_normal((ncols, n)) / np.sqrt(n)).astype(np.float16)
+    dec = v.astype(np.float64)
+    Wv = rng.standard_normal((k, n))
+    V16 = torch.from_numpy(v.view(np.uint8)).cuda()
+    Wd = torch.from_numpy(Wv).cuda()
+    Ht = cb.basis_dot_multi("f16", n, V16, n, np.ones(ncols), Wd, path="tensor").cpu().numpy()
+    Hc = cb.basis_dot_multi("f16", n, V16, n, np.ones(ncols), Wd, path="cuda").cpu().numpy()
+    scale = np.linalg.norm(dec, axis=1)[:, None] * np.linalg.norm(Wv, axis=1)[None, :]
+    assert np.all(np.abs(Ht - Hc) <= 2e-13 * scale)
+    for t in range(40):
+        c, r = int(rng.integers(ncols)), int(rng.integers(k))
+        ref = O.dot(dec[c], Wv[r])
+        assert abs(Ht[c, r] - ref) <= 1e-13 * scale[c, r], (c, r)
