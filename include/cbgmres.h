@@ -52,15 +52,19 @@ typedef enum {
 typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2, CBG_PC_BJ4 = 3 } cbg_precond;
 typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
 
-/* Arithmetic of the basis products (Fig. 1 steps 5, 8, 17).
+/* Arithmetic of the basis products (Fig. 1 steps 5, 8, 17) and of the per-step SpMV
+ * (step 3).
  * CBG_ARITH_DF32: products and partial sums in double-float (pairs of FP32 with
  *   error-free transformations, >= 44-bit effective significand per partial chain),
- *   cross-thread and cross-block combination in FP64.  GB300's FP64 pipe issues about
- *   1/70 of its FP32 rate, so this is the mode that streams the basis at HBM speed.
+ *   cross-thread and cross-block combination in FP64.  The per-step SpMV forms each
+ *   product val * x exactly as an FP32 pair from the values split once into FP32 hi / lo
+ *   planes (a relative 2^-48 perturbation of A) and delivers w as such planes.  GB300's
+ *   FP64 pipe issues about 1/70 of its FP32 rate, so this is the mode that streams the
+ *   basis at HBM speed.
  * CBG_ARITH_FP64: every product and sum is a native FP64 operation, as the paper
  *   prescribes; on GB300 the basis products then run at FP64-pipe speed.
- * SpMV, norms, Givens rotations, the least-squares solve and the solution update are
- * FP64 in both modes. */
+ * The residual SpMV (b - Ax, the convergence judge), norms, Givens rotations, the
+ * least-squares solve and the solution update are FP64 in both modes. */
 typedef enum { CBG_ARITH_DF32 = 0, CBG_ARITH_FP64 = 1 } cbg_arith;
 
 /* status codes */
