@@ -167,10 +167,10 @@ int cbgmres_format_bytes(int fmt);
 
 /* Create a solver for A with restart length `restart` (basis dimension m, Fig. 1) and
  * basis format `fmt`.  Copies A to library-owned device memory and allocates the basis
- * V ((m+1) columns of n codes, each column 2048-element padded), the per-vector scales,
- * the Hessenberg and the work vectors once; every solve reuses them.
- * Errors: CBG_ERR_ARG (n < 1, restart < 1, bad format, bad CSR bounds when the CSR is
- * on the host), CBG_ERR_OOM, CBG_ERR_CUDA.  *out is NULL on error. */
+ * V ((m+1) columns of n codes, each column padded to a multiple of 4096 elements), the
+ * per-vector scales, the Hessenberg and the work vectors once; every solve reuses them.
+ * Errors: CBG_ERR_ARG (n < 1, restart < 1 or > 255, bad format, bad CSR bounds when the
+ * CSR is on the host), CBG_ERR_OOM, CBG_ERR_CUDA.  *out is NULL on error. */
 int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* opt,
                    cbg_handle** out);
 
