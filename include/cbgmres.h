@@ -58,7 +58,12 @@ typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEV
  *   error-free transformations, >= 44-bit effective significand per partial chain),
  *   cross-thread and cross-block combination in FP64.  The per-step SpMV forms each
  *   product val * x exactly as an FP32 pair from the values split once into FP32 hi / lo
- *   planes (a relative 2^-48 perturbation of A) and delivers w as such planes.  GB300's
+ *   planes (a relative 2^-48 perturbation of A) and delivers w as such planes.  The
+ *   per-step operator (A, or A D^{-1} under Jacobi) is normalised by a power of two so
+ *   that its largest |value| lies in [1, 2) and the FP32 pairs stay far from underflow
+ *   and overflow at any matrix scale; the Hessenberg columns are scaled back exactly.
+ *   An operator whose smallest nonzero |value| is below 2^-64 of its largest keeps FP64
+ *   products in that SpMV.  GB300's
  *   FP64 pipe issues about 1/70 of its FP32 rate, so this is the mode that streams the
  *   basis at HBM speed.
  * CBG_ARITH_FP64: every product and sum is a native FP64 operation, as the paper
@@ -285,7 +290,9 @@ int cbgmres_spmv(cbg_handle* h, const double* x, double* y);
  * device work queue hands out systems in decreasing size; systems with at least
  * `split_rows` rows are solved by a whole cluster (rows split across its blocks, sums
  * through distributed shared memory), smaller ones by single blocks.  With
- * options.use_graph the launch is replayed from a CUDA graph.
+ * options.use_graph the launch is replayed from a CUDA graph.  Each system's per-step
+ * operator is normalised and its SpMV runs in double-float under the rules cbg_arith
+ * describes (f64 bases keep FP64 products in that SpMV).
  * Vectors are packed: system s occupies entries [off_s, off_s + n_s) with off_s the sum
  * of the sizes of systems 0..s-1 (the order of As).  Errors: CBG_ERR_ARG (bad CSR,
  * restart > 64), CBG_ERR_UNSUPPORTED (other options), CBG_ERR_OOM, CBG_ERR_CUDA. */

@@ -84,6 +84,7 @@ struct cbg_batch {
     int* d_order = nullptr;
     int *d_rowptr = nullptr, *d_col = nullptr;
     double *d_val = nullptr, *d_valp = nullptr, *d_dinv = nullptr;
+    float* d_valpdf = nullptr;   // the per-step SpMV's values as FP32 hi / lo planes (or null)
     unsigned char* d_V = nullptr;
     BatchOut* d_out = nullptr;
     unsigned int* d_queue = nullptr;
@@ -115,11 +116,41 @@ size_t smem_bytes(const cbg_batch* bt, const Schedule& sc)
     return sizeof(BtSmem) + (size_t)(rows + 32) * sizeof(float2);
 }
 
+// Per system: the power of two 2^s that brings the largest |value| of its per-step operator
+// into [1, 2), and whether that normalised operator's smallest nonzero |value| is at least
+// 2^-64 (its double-float products then stay far from FP32 underflow).
+int normalising_exponent(const double* v, long long n, bool& df_ok)
+{
+    double vmax = 0.0, vmin = INFINITY;
+    for (long long p = 0; p < n; p++) {
+        const double a = std::fabs(v[p]);
+        vmax = std::max(vmax, a);
+        if (a != 0.0) vmin = std::min(vmin, a);
+    }
+    if (vmax == 0.0) return 0;
+    const int e = std::max(-960, std::min(960, -std::ilogb(vmax)));
+    if (std::ldexp(vmin, e) < 0x1p-64) df_ok = false;
+    return e;
+}
+
+// The values times 2^e (exact) as FP32 planes hi[n] then lo[n] with hi = RN(x) and
+// lo = RN(x - hi) (the difference is exact in FP64), so |hi + lo - x| <= 2^-48 |x|.
+void split_values_df(const double* v, long long n, int e, float* hi, float* lo)
+{
+    for (long long p = 0; p < n; p++) {
+        const double x = std::ldexp(v[p], e);
+        const float h = (float)x;
+        hi[p] = h;
+        lo[p] = (float)(x - (double)h);
+    }
+}
+
 void free_batch(cbg_batch* bt)
 {
     if (!bt) return;
     cudaFree(bt->d_sys); cudaFree(bt->d_order); cudaFree(bt->d_rowptr); cudaFree(bt->d_col);
-    cudaFree(bt->d_val); cudaFree(bt->d_valp); cudaFree(bt->d_dinv); cudaFree(bt->d_V); cudaFree(bt->d_out);
+    cudaFree(bt->d_val); cudaFree(bt->d_valp); cudaFree(bt->d_dinv); cudaFree(bt->d_valpdf);
+    cudaFree(bt->d_V); cudaFree(bt->d_out);
     cudaFree(bt->d_queue); cudaFree(bt->d_io);
     if (bt->h_io) cudaFreeHost(bt->h_io);
     if (bt->graph) cudaGraphExecDestroy(bt->graph);
@@ -141,6 +172,8 @@ BatchArgs make_args(const cbg_batch* bt, const Schedule& sc, double tol, long lo
     a.valp = bt->d_valp ? bt->d_valp : bt->d_val;
     a.val = bt->d_val;
     a.dinv = bt->d_dinv;
+    a.valpdf = bt->d_valpdf;
+    a.nnz_all = bt->total_nnz;
     a.io = bt->d_io;
     a.V = bt->d_V;
     a.out = bt->d_out;
@@ -309,6 +342,8 @@ int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt, co
         d.nz_off = (long long)ci_all.size();
         d.vec_off = vec_off;
         d.v_off = v_off;
+        d.pscale = 1.0;
+        d.hscale = 1.0;
         v_off += (long long)(restart + 1) * d.ld * bs;
         v_off = (v_off + 255) / 256 * 256;
         vec_off += A.n;
@@ -341,7 +376,6 @@ int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt, co
         return CBG_OK;
     };
     int rc = CBG_OK;
-    rc = rc ? rc : up((void**)&bt->d_sys, bt->sys.data(), bt->sys.size() * sizeof(BatchSys));
     rc = rc ? rc : up((void**)&bt->d_order, bt->order.data(), bt->order.size() * sizeof(int));
     rc = rc ? rc : up((void**)&bt->d_rowptr, rp_all.data(), rp_all.size() * sizeof(int));
     rc = rc ? rc : up((void**)&bt->d_col, ci_all.data(), ci_all.size() * sizeof(int));
@@ -350,6 +384,29 @@ int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt, co
         rc = rc ? rc : up((void**)&bt->d_valp, vp_all.data(), vp_all.size() * sizeof(double));
         rc = rc ? rc : up((void**)&bt->d_dinv, di_all.data(), di_all.size() * sizeof(double));
     }
+    // each system's per-step operator normalised by a power of two (w = A v then stays near
+    // unit size, far from FP32 underflow and overflow in the double-float sums; the
+    // Hessenberg columns are scaled back exactly), and its values as double-float planes
+    // unless some system's dynamic range exceeds 2^64 (FP64 products then)
+    {
+        const std::vector<double>& vs = o.precond == CBG_PC_JACOBI ? vp_all : va_all;
+        bool df_ok = true;
+        std::vector<int> ex(nsys);
+        for (int i = 0; i < nsys; i++) {
+            BatchSys& d = bt->sys[i];
+            ex[i] = normalising_exponent(vs.data() + d.nz_off, As[i].nnz, df_ok);
+            d.pscale = std::ldexp(1.0, ex[i]);
+            d.hscale = std::ldexp(1.0, -ex[i]);
+        }
+        if (!rc && df_ok && fmt != CBG_F64) {       // (f64 codes keep FP64 products)
+            std::vector<float> df(2 * vs.size());
+            for (int i = 0; i < nsys; i++)
+                split_values_df(vs.data() + bt->sys[i].nz_off, As[i].nnz, ex[i], df.data() + bt->sys[i].nz_off,
+                                df.data() + vs.size() + bt->sys[i].nz_off);
+            rc = up((void**)&bt->d_valpdf, df.data(), df.size() * sizeof(float));
+        }
+    }
+    rc = rc ? rc : up((void**)&bt->d_sys, bt->sys.data(), bt->sys.size() * sizeof(BatchSys));
     if (!rc && cudaMalloc((void**)&bt->d_V, std::max<long long>(v_off, 256)) != cudaSuccess) rc = CBG_ERR_OOM;
     if (!rc && cudaMemset(bt->d_V, 0, std::max<long long>(v_off, 256)) != cudaSuccess) rc = CBG_ERR_CUDA;
     if (!rc && cudaMalloc((void**)&bt->d_out, nsys * sizeof(BatchOut)) != cudaSuccess) rc = CBG_ERR_OOM;

@@ -31,6 +31,8 @@ struct BatchSys {
     long long nz_off;       // offset of its nonzeros (column indices are local)
     long long vec_off;      // offset of its b / x / dinv entries
     long long v_off;        // byte offset of its basis
+    double pscale;          // 2^s normalising its per-step operator (largest |value| in [1, 2))
+    double hscale;          // 2^-s: Hessenberg columns back to the unscaled operator
 };
 
 struct BatchOut {
@@ -51,6 +53,10 @@ struct BatchArgs {
     const double* valp;     // A D^{-1} (Jacobi) or A
     const double* val;      // A
     const double* dinv;     // D^{-1} or null
+    const float* valpdf;    // valp times each system's pscale as FP32 hi [nnz_all] then lo
+                            // [nnz_all] planes for the per-step SpMV in double-float, or null
+                            // (FP64 products)
+    long long nnz_all;
     double* const* io;      // io[0] = b (packed), io[1] = x (packed); device table
     unsigned char* V;
     BatchOut* out;
@@ -184,6 +190,78 @@ template <int FMT> struct BatchedSolver {
             }
         }
         return ss;
+    }
+
+    // The per-step w = A_pc v_j in double-float: every product val * code is formed as an
+    // FP32 pair (TwoProd on the split values; exact for single-float codes up to the
+    // rounding of the lo term) and summed with TwoSum; w goes to ws as its renormalised
+    // pair and the sum of w^2 is accumulated in double-float, so no FP64 operation runs
+    // per nonzero or per row (GB300's FP64 pipe is ~70x narrower than its FP32 pipe).
+    // The planes hold the normalised operator 2^s A_pc.
+    static __device__ double spmv_df(const BatchArgs& a, const BatchSys& s, BtSmem* sm, int r0, int r1,
+                                     const void* x, double xscale)
+    {
+        const int* rp = a.rowptr + s.rp_off;
+        const int* ci = a.col + s.nz_off;
+        const float* vh = a.valpdf + s.nz_off;
+        const float* vl = a.valpdf + a.nnz_all + s.nz_off;
+        const bool xsplit = xscale != 1.0;                 // unit scale (float formats): no product
+        float xsh = 1.f, xsl = 0.f;
+        if (xsplit) split_f64(xscale, xsh, xsl);
+        float ssS = 0.f, ssC = 0.f;
+        constexpr int RW = 4;                              // rows per thread in flight
+        for (int rb = r0 + threadIdx.x; rb < r1; rb += RW * BT_THREADS) {
+            float S[RW], C[RW];
+            int p0[RW], p1[RW];
+#pragma unroll
+            for (int q = 0; q < RW; q++) {
+                const int r = rb + q * BT_THREADS;
+                S[q] = 0.f;
+                C[q] = 0.f;
+                p0[q] = r < r1 ? rp[r] : 0;
+                p1[q] = r < r1 ? rp[r + 1] : 0;
+            }
+            int len = 0;
+#pragma unroll
+            for (int q = 0; q < RW; q++) len = max(len, p1[q] - p0[q]);
+            for (int i = 0; i < len; i++) {
+#pragma unroll
+                for (int q = 0; q < RW; q++) {
+                    const int p = p0[q] + i;
+                    if (p < p1[q]) {
+                        float xh, xl;
+                        xval_df<FMT>(x, ci[p], xh, xl);
+                        if constexpr (SingleFloat<FMT>::value) df_mac(S[q], C[q], xh, vh[p], vl[p]);
+                        else df_mac2(S[q], C[q], xh, xl, vh[p], vl[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RW; q++) {
+                const int r = rb + q * BT_THREADS;
+                if (r < r1) {
+                    float hi, lo;
+                    two_sum(S[q], C[q], hi, lo);             // renormalise
+                    if (xsplit) {                            // (hi + lo) * (xsh + xsl)
+                        const float p = __fmul_rn(hi, xsh);
+                        float e = __fmaf_rn(hi, xsh, -p);
+                        e = __fmaf_rn(hi, xsl, e);
+                        e = __fmaf_rn(lo, xsh, e);
+                        two_sum(p, e, hi, lo);
+                    }
+                    sm->ws[r - r0] = make_float2(hi, lo);
+                    // w^2 = hi^2 + 2 hi lo to double-float accuracy
+                    const float p = __fmul_rn(hi, hi);
+                    float e = __fmaf_rn(hi, hi, -p);
+                    e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
+                    float t, te;
+                    two_sum(ssS, p, t, te);
+                    ssC = __fadd_rn(ssC, __fadd_rn(te, e));
+                    ssS = t;
+                }
+            }
+        }
+        return df_to_double(ssS, ssC);
     }
 
     // partial h_k = sum over own rows of dec(V_k) w, k < ncols, into sm->red[0..ncols)
@@ -389,8 +467,13 @@ template <int FMT> struct BatchedSolver {
                     team.sync();                               // column j of all blocks visible
                     // w = A D^{-1} v_j (Jacobi folded into the values), omega
                     double om[1];
-                    om[0] = spmv<true>(a, s, sm, r0, r1, a.V + s.v_off + (long long)j * s.ld * BS, sm->scale[j],
-                                       a.valp, false);
+                    // (double-float products unless the planes are absent; f64 codes keep FP64
+                    // products, which measured faster than splitting every gathered code)
+                    const unsigned char* vj = a.V + s.v_off + (long long)j * s.ld * BS;
+                    if (FMT != F64 && a.valpdf)
+                        om[0] = spmv_df(a, s, sm, r0, r1, vj, sm->scale[j]);   // planes hold 2^s A_pc
+                    else
+                        om[0] = spmv<true>(a, s, sm, r0, r1, vj, __dmul_rn(sm->scale[j], s.pscale), a.valp, false);
                     __syncthreads();
                     block_sum<1>(sm, om, 1, j + 1);              // red[j+1] = omega^2 partial
                     dot(a, s, sm, r0, r1, j + 1);                // red[0..j]
@@ -426,20 +509,22 @@ template <int FMT> struct BatchedSolver {
                         for (int r = 0; r < team.size; r++) wmax = fmax(wmax, cl.map_shared_rank(sm->red, r)[1]);
                         cl.sync();
                     }
-                    // Hessenberg column, Givens rotations, stopping tests (identical in every block)
+                    // Hessenberg column (scaled back from the normalised operator, exactly),
+                    // Givens rotations, stopping tests (identical in every block)
                     if (threadIdx.x == 0) {
                         double* Hc = sm->H + j * (m + 1);
-                        for (int i = 0; i <= j; i++) Hc[i] = __dadd_rn(sm->h[i], sm->u[i]);
-                        Hc[j + 1] = hn;
+                        for (int i = 0; i <= j; i++) Hc[i] = __dmul_rn(__dadd_rn(sm->h[i], sm->u[i]), s.hscale);
+                        const double hnt = __dmul_rn(hn, s.hscale);
+                        Hc[j + 1] = hnt;
                         double r0v = Hc[0];
                         for (int i = 0; i < j; i++) {
                             const double c = sm->cs[i], sn = sm->sn[i], r1v = Hc[i + 1];
                             Hc[i] = __dadd_rn(__dmul_rn(c, r0v), __dmul_rn(sn, r1v));
                             r0v = __dadd_rn(__dmul_rn(-sn, r0v), __dmul_rn(c, r1v));
                         }
-                        const double rr = hypot(r0v, hn);
+                        const double rr = hypot(r0v, hnt);
                         double c = 1.0, sn = 0.0;
-                        if (rr != 0.0) { c = r0v / rr; sn = hn / rr; }
+                        if (rr != 0.0) { c = r0v / rr; sn = hnt / rr; }
                         sm->cs[j] = c;
                         sm->sn[j] = sn;
                         Hc[j] = rr;
@@ -449,8 +534,8 @@ template <int FMT> struct BatchedSolver {
                         sm->g[j] = __dmul_rn(c, gj);
                         const double est = fabs(sm->g[j + 1]);
                         int stop = 0;
-                        if (!isfinite(hn) || !isfinite(omega) || !isfinite(est)) stop = 3;
-                        else if (!(hn > a.eps_bd * omega)) stop = 2;
+                        if (!isfinite(hnt) || !isfinite(omega) || !isfinite(est)) stop = 3;
+                        else if (!(hn > a.eps_bd * omega)) stop = 2;        // both of the scaled operator
                         else if (est <= target) stop = 1;
                         else if (j + 1 >= kcap) stop = 4;
                         sm->stop = stop;

@@ -313,6 +313,27 @@ template <int FMT> __device__ __forceinline__ double code_value(const void* base
     } else return f32_to_f64_exact(dec_i16((int)reinterpret_cast<const short*>(base)[i]));
 }
 
+// One code (or FP64 vector entry) as an FP32 pair with x = xh + xl: exact for every
+// format except FP64 vectors and f64 codes (relative error below 2^-48 there).
+template <int XFMT> __device__ __forceinline__ void xval_df(const void* x, int c, float& xh, float& xl)
+{
+    if constexpr (XFMT < 0 || XFMT == F64) {
+        split_f64(reinterpret_cast<const double*>(x)[c], xh, xl);
+    } else if constexpr (XFMT == I32) {
+        dec_i32(reinterpret_cast<const int*>(x)[c], xh, xl);
+    } else {
+        if constexpr (XFMT == F32) xh = reinterpret_cast<const float*>(x)[c];
+        else if constexpr (XFMT == F16) xh = __half2float(reinterpret_cast<const __half*>(x)[c]);
+        else if constexpr (XFMT == BF16)
+            xh = __uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(x)[c]) << 16);
+        else if constexpr (XFMT == E4M3) {
+            float b;
+            dec_e4m3x2(reinterpret_cast<const unsigned char*>(x)[c], xh, b);
+        } else xh = dec_i16((int)reinterpret_cast<const short*>(x)[c]);
+        xl = 0.f;
+    }
+}
+
 // ------------------------------------------------------------------------- encoding
 // Per-vector encode parameters, computed once from vmax = max_i |v_i| (Section 4.2 and
 // the bf16/e4m3 power-of-two scale).  `scale` is what decoding multiplies by.
@@ -320,6 +341,9 @@ struct EncParams {
     double scale;     // sigma (int), 2^e (bf16/e4m3), 1 otherwise
     double inv;       // 1/sigma (int) or 2^-e (bf16/e4m3)
 };
+
+// 2^e as an FP64 value built from its bits, for |e| <= 1022
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
 __host__ __device__ inline int pow2_exponent_for(double vmax, double fmax)
 {   // smallest integer e with vmax <= fmax * 2^e, at least -126

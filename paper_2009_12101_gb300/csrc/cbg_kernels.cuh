@@ -601,6 +601,8 @@ struct StoreArgs {
     long long n;
     int fmt;
     unsigned int* counter;    // last-block counter (mode 0: the last block runs the finalize)
+    int hexp;                 // mode 0: the column (h, ||w||) came from the operator scaled by
+                              // 2^-hexp; the Hessenberg column is it times 2^hexp (0: as is)
 };
 
 
@@ -620,11 +622,16 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     DevState* st = a.d.st;
     const int j = a.j, ldh = st->m + 1;
     const int lane = threadIdx.x & 31;
+    // back from the power-of-two normalised operator (exact)
+    const double hs = a.hexp ? pow2d(a.hexp) : 1.0;
+    hn = __dmul_rn(hn, hs);
+    const double omega = __dmul_rn(st->omega, hs);
     for (int i = lane; i <= j + 1; i += 32) {
         double hv = 0.0;
         if (i <= j) {
             hv = __ldcg(a.d.h + i);
             if (a.reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
+            hv = __dmul_rn(hv, hs);
         } else {
             hv = hn;
         }
@@ -689,8 +696,8 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         if (a.reorth) st->reorths += 1;
         if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
         int stop = 0;
-        if (!isfinite(hn) || !isfinite(st->omega) || !isfinite(est)) stop = 3;
-        else if (!(hn > st->eps_bd * st->omega)) stop = 2;
+        if (!isfinite(hn) || !isfinite(omega) || !isfinite(est)) stop = 3;
+        else if (!(hn > st->eps_bd * omega)) stop = 2;
         else if (est <= st->target) stop = 1;
         else if (j + 1 >= st->kcap) stop = 4;
         if (stop) {
@@ -776,28 +783,10 @@ struct SpmvArgs {
     // summed in double-float (may be null)
     const float* valdf;
     long long nnz;
+    // Arnoldi, FP64 rows: y = 2^xexp A x, the operator normalised by a power of two (the
+    // split planes valdf hold it already scaled)
+    int xexp;
 };
-
-// One code (or FP64 vector entry) as an FP32 pair with x = xh + xl: exact for every
-// format except FP64 vectors and f64 codes (relative error below 2^-48 there).
-template <int XFMT> __device__ __forceinline__ void xval_df(const void* x, int c, float& xh, float& xl)
-{
-    if constexpr (XFMT < 0 || XFMT == F64) {
-        split_f64(reinterpret_cast<const double*>(x)[c], xh, xl);
-    } else if constexpr (XFMT == I32) {
-        dec_i32(reinterpret_cast<const int*>(x)[c], xh, xl);
-    } else {
-        if constexpr (XFMT == F32) xh = reinterpret_cast<const float*>(x)[c];
-        else if constexpr (XFMT == F16) xh = __half2float(reinterpret_cast<const __half*>(x)[c]);
-        else if constexpr (XFMT == BF16)
-            xh = __uint_as_float(((unsigned int)reinterpret_cast<const unsigned short*>(x)[c]) << 16);
-        else if constexpr (XFMT == E4M3) {
-            float b;
-            dec_e4m3x2(reinterpret_cast<const unsigned char*>(x)[c], xh, b);
-        } else xh = dec_i16((int)reinterpret_cast<const short*>(x)[c]);
-        xl = 0.f;
-    }
-}
 
 template <int XFMT, int GROUP, int MODE>
 __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
@@ -807,7 +796,8 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     const int lane_g = threadIdx.x & (GROUP - 1);
     const long long gid = ((long long)blockIdx.x * THREADS + threadIdx.x) / GROUP;
     const long long ngroups = (long long)gridDim.x * THREADS / GROUP;
-    const double xs = a.xscale_dev ? *a.xscale_dev : a.xscale;
+    double xs = a.xscale_dev ? *a.xscale_dev : a.xscale;
+    if (a.xexp) xs = __dmul_rn(xs, pow2d(a.xexp));
     double ss = 0.0;
     unsigned long long mxb = 0;
     auto xval = [&](int c) -> double {

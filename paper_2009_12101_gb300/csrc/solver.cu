@@ -124,6 +124,39 @@ __global__ void k_split_df(const double* w, long long n, float* out)
     }
 }
 
+// largest |v| and smallest nonzero |v| as FP64 bit patterns (non-negative doubles order as
+// integers); mm = {max, min} must start as {0, ~0}
+__global__ void k_abs_range(const double* v, long long n, unsigned long long* mm)
+{
+    unsigned long long mx = 0ull, mn = ~0ull;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v[i]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+        if (b != 0ull) mn = b < mn ? b : mn;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ox = __shfl_xor_sync(0xFFFFFFFFu, mx, o), on = __shfl_xor_sync(0xFFFFFFFFu, mn, o);
+        mx = ox > mx ? ox : mx;
+        mn = on < mn ? on : mn;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(mm, mx);
+        if (mn != ~0ull) atomicMin(mm + 1, mn);
+    }
+}
+
+// out = the values times 2^e (exact) as double-float hi / lo planes
+__global__ void k_split_df_pow2(const double* v, long long n, int e, float* out)
+{
+    const double sc = pow2d(e);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float h, l;
+        split_f64(__dmul_rn(v[i], sc), h, l);
+        out[i] = h;
+        out[n + i] = l;
+    }
+}
+
 __global__ void k_jacobi_prepare(const int* rowptr, const int* col, const double* val, long long n,
                                  double* dinv, int* bad)
 {
@@ -342,7 +375,9 @@ struct cbg_handle {
     int* col = nullptr;
     double* val = nullptr;     // A
     double* valp = nullptr;    // A D^{-1} (Jacobi) or nullptr
-    float* valdf = nullptr;    // the Arnoldi SpMV's values (valp or val) as FP32 hi / lo planes
+    float* valdf = nullptr;    // the Arnoldi SpMV's values (valp or val) times 2^pexp as FP32
+                               // hi / lo planes, or null (FP64 products)
+    int pexp = 0;              // the per-step operator is normalised by 2^pexp
     double* dinv = nullptr;    // D^{-1}
     double* pvals = nullptr;   // values of P: SPAI (A's pattern) or block-Jacobi inverse blocks
     int* prow = nullptr;       // P's pattern: A's for SPAI, the diagonal blocks for block-Jacobi
@@ -539,6 +574,7 @@ void enqueue_step(cbg_handle* h, int j)
             a.ydf_ld = h->ld;
             a.valdf = wdf ? h->valdf : nullptr;
             a.nnz = h->nnz;
+            a.xexp = a.valdf ? 0 : h->pexp;          // (the planes hold the scaled values)
             a.counter = h->d.counters + 1;
             launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
         }
@@ -612,6 +648,7 @@ void enqueue_step(cbg_handle* h, int j)
     sa.n = h->n;
     sa.fmt = h->fmt;
     sa.counter = h->d.counters + 6;
+    sa.hexp = -h->pexp;
     launch(h, 3, store_bytes(h), [&] { op.store(h->grid_store, s, sa); });
 }
 
@@ -919,10 +956,33 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
         if (hbad) TRY(CBG_ERR_ARG);
     }
-    // values of the per-step SpMV split for double-float products
-    TRY(dalloc(&h->valdf, 2 * nnz));
-    k_split_df<<<2048, 256>>>(h->valp ? h->valp : h->val, nnz, h->valdf);
-    if (cudaGetLastError() != cudaSuccess) TRY(CBG_ERR_CUDA);
+    // The per-step operator (A D^{-1} under Jacobi, else A) is normalised by a power of two,
+    // 2^pexp, so that its largest |value| lies in [1, 2): w = A v then stays near unit size
+    // and the double-float products and sums of squares stay far from FP32 underflow and
+    // overflow whatever the matrix's scale.  The Hessenberg columns are scaled back
+    // exactly.  (SPAI and block Jacobi apply an approximate inverse first: A P is already
+    // normalised.)  Its values are split into double-float planes unless their dynamic
+    // range exceeds 2^64 (FP64 products then).
+    {
+        const bool norm = o.precond == CBG_PC_NONE || o.precond == CBG_PC_JACOBI;
+        const double* vs = h->valp ? h->valp : h->val;
+        unsigned long long* mm = (unsigned long long*)h->scratch;
+        const unsigned long long init[2] = {0ull, ~0ull};
+        unsigned long long hm[2] = {0ull, 0ull};
+        if (cudaMemcpy(mm, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        k_abs_range<<<1024, 256>>>(vs, nnz, mm);
+        if (cudaMemcpy(hm, mm, sizeof(hm), cudaMemcpyDeviceToHost) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        double vmax = 0.0, vmin = 0.0;
+        std::memcpy(&vmax, &hm[0], sizeof(double));
+        std::memcpy(&vmin, &hm[1], sizeof(double));
+        h->pexp = norm && vmax > 0.0 ? std::max(-960, std::min(960, -std::ilogb(vmax))) : 0;
+        const double smax = std::ldexp(vmax, h->pexp), smin = std::ldexp(vmin, h->pexp);
+        if (vmax == 0.0 || (smin >= 0x1p-64 && smax <= 0x1p32)) {
+            TRY(dalloc(&h->valdf, 2 * nnz));
+            k_split_df_pow2<<<2048, 256>>>(vs, nnz, h->pexp, h->valdf);
+        }
+        if (cudaGetLastError() != cudaSuccess) TRY(CBG_ERR_CUDA);
+    }
     h->prow = h->rowptr;
     h->pcol = h->col;
     if (o.precond == CBG_PC_BJ4) {

@@ -29,3 +29,18 @@ def col_relerr(Hg, Ho, k):
         a = Hg[: j + 2, j]; b = Ho[: j + 2, j]
         out.append(np.linalg.norm(a - b) / np.linalg.norm(b))
     return np.array(out)
+
+
+def scaled_matrix(A, case):
+    """A test matrix outside the usual scale: A times 2^-70 ("tiny") or 2^40 ("huge"), which
+    the solvers normalise by a power of two, or with every 50th off-diagonal nonzero
+    times 2^-80 ("wide": a dynamic range beyond 2^64, where the per-step SpMV keeps FP64
+    products); "one" leaves A as it is."""
+    import workloads as W
+    v = A.val.copy()
+    if case == "wide":
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        v[np.flatnonzero(A.col != rows)[::50]] *= 2.0 ** -80
+    else:
+        v *= {"one": 1.0, "tiny": 2.0 ** -70, "huge": 2.0 ** 40}[case]
+    return W.CSR(A.n, A.rowptr, A.col, v)

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_common import need_gpu
+from gpu_common import need_gpu, scaled_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -18,13 +18,13 @@ def _batch(nsys, nmin, nmax, seed=4):
     return mats, bs
 
 
-def _check_against_oracle(mats, bs, x, out, fmt, tol, m=30):
+def _check_against_oracle(mats, bs, x, out, fmt, tol, m=30, precond=O.PC_JACOBI):
     f = O.FORMATS[fmt]
     off = 0
     for i, (A, b) in enumerate(zip(mats, bs)):
         xi = x[off:off + A.n]
         off += A.n
-        ro = O.gmres(A, b, m=m, fmt=f, precond=O.PC_JACOBI, tol=tol, maxit=100000)
+        ro = O.gmres(A, b, m=m, fmt=f, precond=precond, tol=tol, maxit=100000)
         assert ro["status"] == O.OK
         assert out["statuses"][i] == 0, (i, out["statuses"][i])
         res = np.linalg.norm(b - O.spmv(A, xi)) / np.linalg.norm(b)
@@ -47,6 +47,23 @@ def test_batched_matches_oracle(fmt, schedule, use_graph):
             out = bt.solve(b, x, tol=1e-8)
             assert out["status"] == 0
         _check_against_oracle(mats, bs, x.cpu().numpy(), out, fmt, 1e-8)
+
+
+@pytest.mark.parametrize("case", ["one", "tiny", "huge", "wide"])
+def test_batched_without_preconditioner(case):
+    """No preconditioner, restart 64: the per-step SpMV takes A's own values, normalised by a
+    power of two per system (tiny, huge) or kept in FP64 (wide dynamic range); each system
+    against the oracle on the same matrix."""
+    torch, cb = need_gpu()
+    mats, _ = _batch(10, 200, 1200, seed=9)
+    mats = [scaled_matrix(A, case) for A in mats]
+    bs = [W.rhs_from_solution(A, W.exact_solution(A.n, 4, salt=i)) for i, A in enumerate(mats)]
+    with cb.BatchedSolver(mats, restart=64, fmt="f32", precond="none") as bt:
+        b = torch.from_numpy(np.concatenate(bs)).cuda()
+        x = torch.zeros(bt.total, dtype=torch.float64, device="cuda")
+        out = bt.solve(b, x, tol=1e-8)
+        assert out["status"] == 0
+    _check_against_oracle(mats, bs, x.cpu().numpy(), out, "f32", 1e-8, m=64, precond=O.PC_NONE)
 
 
 def test_batched_zero_rhs_and_tuner(tmp_path):

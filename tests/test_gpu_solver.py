@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_common import FORMATS, col_relerr, need_gpu, to_dev
+from gpu_common import FORMATS, col_relerr, need_gpu, scaled_matrix, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +38,32 @@ def test_hessenberg_first_columns(prob, fmt, arith):
     assert Hg.shape == (k + 1, k)
     err = col_relerr(Hg, ro["H1"], k)
     assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("arith", ["df32", "fp64"])
+@pytest.mark.parametrize("case", ["tiny", "huge", "wide"])
+def test_operator_scale_and_range(case, arith):
+    """The matrix times 2^-70 or 2^40 (the solver normalises the per-step operator by a
+    power of two and scales the Hessenberg columns back), or with every 50th off-diagonal
+    nonzero times 2^-80 (a dynamic range beyond 2^64: FP64 products in the per-step SpMV): the
+    first Hessenberg columns against the oracle on the same matrix, and the solve to 1e-10
+    judged by the oracle's SpMV."""
+    torch, cb = need_gpu()
+    A0, xs, _ = _problem("convdiff20")
+    A = scaled_matrix(A0, case)
+    b = W.rhs_from_solution(A, xs)
+    k = 10
+    ro = O.gmres(A, b, m=20, fmt=O.F32, tol=0.0, maxit=k, want_H1=True)
+    with cb.Solver.from_csr(A, restart=20, fmt="f32", arith=arith) as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+        err = col_relerr(Hg, ro["H1"], k)
+        assert np.all(err <= 1e-10), err
+    with cb.Solver.from_csr(A, restart=100, fmt="f32", arith=arith) as s:
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(to_dev(torch, b), xg, tol=1e-10, maxit=20000)
+    assert st["status"] == 0, st
+    r = b - O.spmv(A, xg.cpu().numpy())
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
 
 
 @pytest.mark.parametrize("fmt", FORMATS)
