@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
+    p.add_argument("--batch-nsys", type=int, default=512,
+                   help="systems of the batch workload (512 is the benchmark; fewer for profiling)")
+    p.add_argument("--schedule", type=int, nargs=2, metavar=("CLUSTER", "SPLIT_ROWS"),
+                   help="batch workload: this schedule instead of autotuning (for profiling)")
     p.add_argument("--workload", choices=["convdiff128", "batch512", "random27", "learned96", "restart_sweep",
                                           "multirhs"],
                    default="convdiff128")
@@ -226,7 +230,7 @@ def run_batch(args):
     import paper_2009_12101_gb300 as cb
     import workloads as W
     cb.ensure_built()
-    mats = W.stencil_batch()
+    mats = W.stencil_batch(nsys=args.batch_nsys)
     xs = [W.exact_solution(A.n, 4, salt=i) for i, A in enumerate(mats)]
     b = np.concatenate([W.rhs_from_solution(A, x) for A, x in zip(mats, xs)])
     fmts = ["f64", "f32", "f16"]
@@ -239,7 +243,11 @@ def run_batch(args):
     for f in fmts:
         solvers[f] = cb.BatchedSolver(mats, restart=m, fmt=f, precond="jacobi", use_graph=True)
         x.zero_()
-        sched[f] = solvers[f].tune(bd, x, tol=tol, cache_path=cache)
+        if args.schedule:
+            solvers[f].schedule(*args.schedule)
+            sched[f] = tuple(args.schedule)
+        else:
+            sched[f] = solvers[f].tune(bd, x, tol=tol, cache_path=cache)
     for _ in range(args.warmup):
         for f in fmts:
             x.zero_(); solvers[f].solve(bd, x, tol=tol)
@@ -292,7 +300,7 @@ def run_batch(args):
         "metric": METRIC, "value": round(t["f64"] / t["f32"], 4), "unit": "x", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "nsys": len(mats), "total_rows": int(b.size), "restart": m,
+        "config": {"workload": BATCH_WORKLOAD.replace("batch512", f"batch{len(mats)}"), "nsys": len(mats), "total_rows": int(b.size), "restart": m,
                    "tol": tol, "formats": fmts, "schedule_cluster_split": {f: list(v) for f, v in sched.items()},
                    "l2": "no flush: basis of the batch (0.5-2 GB) exceeds the 129 MB L2"},
         "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},

@@ -33,7 +33,7 @@ def _check_against_oracle(mats, bs, x, out, fmt, tol, m=30, precond=O.PC_JACOBI)
         assert np.linalg.norm(xi - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"]), i
 
 
-@pytest.mark.parametrize("fmt", ["f32", "f16"])
+@pytest.mark.parametrize("fmt", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("schedule", [(1, 1 << 30), (4, 1500), (8, 3000)])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_batched_matches_oracle(fmt, schedule, use_graph):
