@@ -42,7 +42,7 @@ typedef enum {
     CBG_I16 = 6    /* fixed point, code = rint(v / sigma), sigma = max|v| / (2^15-1) */
 } cbg_format;
 
-/* Right preconditioners M^{-1} (Fig. 1 steps 3 and 17: w = A M^{-1} v, x += M^{-1} V y).
+/* Right preconditioners M^{-1} (Fig. 1: w = A M^{-1} v, x += M^{-1} V y).
  * JACOBI: diagonal scaling, folded into the stored values A D^{-1} (Section 5.1).
  * SPAI:   z = P v with P on A's pattern (cbgmres_set_spai; the learned preconditioner).
  * BJ4:    block-Jacobi with diagonal blocks of 4 consecutive rows (the last block may be
@@ -52,8 +52,8 @@ typedef enum {
 typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2, CBG_PC_BJ4 = 3 } cbg_precond;
 typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
 
-/* Arithmetic of the basis products (Fig. 1 steps 5, 8, 17) and of the per-step SpMV
- * (step 3).
+/* Arithmetic of the basis products (the CGS projection, its re-orthogonalisation and
+ * the solution update of Fig. 1) and of the per-step SpMV.
  * CBG_ARITH_DF32: products and partial sums in double-float (pairs of FP32 with
  *   error-free transformations, >= 44-bit effective significand per partial chain),
  *   cross-thread and cross-block combination in FP64.  The per-step SpMV forms each
@@ -125,7 +125,7 @@ typedef struct {
 } cbg_options;
 
 typedef struct {
-    int64_t iters;           /* Arnoldi steps (sparse products of Fig. 1 step 3)       */
+    int64_t iters;           /* Arnoldi steps (sparse products of Fig. 1)         */
     int64_t restarts;        /* restart cycles started                                 */
     int64_t reorths;         /* re-orthogonalisation passes                            */
     double true_relres;      /* ||b - A x||_2 / ||b||_2 at exit (FP64, explicit)       */
@@ -199,7 +199,7 @@ int cbgmres_solve_host(cbg_handle* h, const double* b_host, double* x_host, doub
 /* Run k Arnoldi steps of the first restart cycle from x0 (device b, x0) and copy the
  * raw (k+1) x k Hessenberg (before Givens rotations, column-major, leading dimension
  * k+1) to H_host.  *k_done receives the number of columns produced (< k on breakdown).
- * Used to check parity of the orthogonalisation (Fig. 1 steps 3-14). */
+ * Used to check parity of the orthogonalisation (the Arnoldi step of Fig. 1). */
 int cbgmres_arnoldi(cbg_handle* h, const double* b, const double* x0, int k,
                     double* H_host, int* k_done);
 
@@ -219,7 +219,7 @@ int cbg_encode(int fmt, int64_t n, const double* v, double vmax, void* codes,
 int cbg_decode(int fmt, int64_t n, const void* codes, double scale, double* out,
                void* stream);
 
-/* ---- basis products, exposed for parity checks (Fig. 1 steps 5 and 8) -------------
+/* ---- basis products, exposed for parity checks (CGS and re-orthogonalisation, Fig. 1) -------------
  * V: device codes, ncols columns of leading dimension ld elements; scales[ncols] host.
  * cbg_basis_dot:  h[k] = sum_i dec(V[i,k]) w[i]      (h: host, w: device)
  * cbg_basis_axpy: w[i] -= sum_k dec(V[i,k]) h[k]     (h: host, w: device, in place)

@@ -315,7 +315,7 @@ static int block_jacobi_inverse(int64_t n, const int32_t* rowptr, const int32_t*
     return 0;
 }
 
-/* z = M^{-1} v  (Fig. 1 step 3 and step 17; right preconditioning) */
+/* z = M^{-1} v  (Fig. 1: the Arnoldi SpMV and the solution update; right preconditioning) */
 static void apply_precond(const problem* P, const double* v, double* z)
 {
     int64_t n = P->n;
@@ -440,7 +440,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
     double last_est = 0.0;       /* recurrence residual the previous cycle ended with   */
     a->promotions = 0;
     for (;;) {
-        /* Fig. 1 step 1: r0 = b - A x0, beta = ||r0|| */
+        /* Fig. 1, cycle start: r0 = b - A x0, beta = ||r0|| */
         or_spmv(n, rowptr, col, val, x, r);
         for (int64_t i = 0; i < n; i++) r[i] = b[i] - r[i];
         double beta = nrm2(n, r);
@@ -474,20 +474,20 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         int nonfinite = 0;
         for (int64_t j = 0; j < kcap; j++) {
             const double* vj = V + (size_t)j * (size_t)n;
-            /* step 3: w = A (M^{-1} v) */
+            /* w = A (M^{-1} v) */
             apply_precond(&P, vj, z);
             or_spmv(n, rowptr, col, val, z, w);
-            /* step 4: omega = ||w|| */
+            /* omega = ||w|| */
             double omega = nrm2(n, w);
-            /* step 5: CGS, h_{1:j,j} = V_j^T w, w = w - V_j h */
+            /* CGS: h_{1:j,j} = V_j^T w, w = w - V_j h */
             for (int64_t i = 0; i <= j; i++) h[i] = or_dot(n, V + (size_t)i * (size_t)n, w);
             for (int64_t i = 0; i <= j; i++) {
                 const double* vi = V + (size_t)i * (size_t)n;
                 for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * h[i];
             }
-            /* step 6: h_{j+1,j} = ||w|| */
+            /* h_{j+1,j} = ||w|| */
             double hn = nrm2(n, w);
-            /* steps 7-11: re-orthogonalise (always, or when h_{j+1,j} < eta omega) */
+            /* re-orthogonalise (always, or when h_{j+1,j} < eta omega) */
             int do_re = a->reorth == OR_REORTH_ALWAYS ||
                         (a->reorth == OR_REORTH_CONDITIONAL && hn < a->eta * omega);
             if (do_re) {
@@ -501,7 +501,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
                 a->reorths++;
             }
             if (!isfinite(hn) || !isfinite(omega)) { nonfinite = 1; break; }
-            /* column j of the (m+1) x m Hessenberg (step 16) */
+            /* column j of the (m+1) x m Hessenberg (Fig. 1) */
             for (int64_t i = 0; i <= j; i++) H[i + j * (m + 1)] = h[i];
             H[j + 1 + j * (m + 1)] = hn;
             a->iters++;
@@ -528,13 +528,13 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             if (a->hist && a->nhist < a->hist_cap) a->hist[a->nhist++] = est / bnorm;
             k = j + 1;
 
-            /* step 12: breakdown (reading R2) or literal clause */
+            /* breakdown (reading R2) or the printed clause */
             int stop = !(hn > a->eps_bd * omega);
             if (a->literal_fig1) stop = (hn == 0.0) || (hn < a->eta * omega);
             if (stop) break;
             /* recurrence residual signals convergence (Section 5.2) */
             if (est <= target) break;
-            /* steps 13-14: v = w / h_{j+1,j}, V_{j+1} = [V_j, v] (stored compressed) */
+            /* v = w / h_{j+1,j}, V_{j+1} = [V_j, v] (stored compressed) */
             if (compress_column(fmt, n, w, hn, codes, V + (size_t)(j + 1) * (size_t)n, tmp)) {
                 nonfinite = 1;
                 break;
@@ -547,7 +547,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             if (a->H1) memcpy(a->H1, H, (size_t)(m + 1) * (size_t)m * sizeof(double));
             if (a->V1) memcpy(a->V1, V, (size_t)n * (size_t)nv * sizeof(double));
         }
-        /* step 17: y = argmin ||beta e1 - H y|| by back substitution on R */
+        /* y = argmin ||beta e1 - H y|| by back substitution on R */
         for (int64_t i = k - 1; i >= 0; i--) {
             double s = g[i];
             for (int64_t c = i + 1; c < k; c++) s -= R[i + c * (m + 1)] * y[c];
@@ -562,7 +562,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
         apply_precond(&P, tmp, z);
         for (int64_t t = 0; t < n; t++) x[t] += z[t];
         if (!all_finite(n, x)) { a->status = OR_ERR_NONFINITE; break; }
-        /* step 18: go to step 1 (the explicit residual decides) */
+        /* restart (the explicit residual decides) */
     }
 done:
     a->fmt_final = fmt;

@@ -14,7 +14,7 @@
  *   - Section 2 (stopping test ||b - A x||_2 <= tau ||b||_2, QR/Givens update of the
  *     Hessenberg least-squares problem);
  *   - Section 3 ("CB-GMRES": basis stored in a compact format, all arithmetic FP64, the
- *     basis decompressed before Lines 5, 8 and 17 of Fig. 1);
+ *     basis decompressed before each product with it in Fig. 1);
  *   - Section 4.2 (memory accessor; fixed-point formats with the per-vector scale
  *     sigma_j = (||v_j||_inf / ||v_j||_2) / max_intxx, applied as a post-multiplication
  *     by diag(Sigma) on every access);
@@ -24,9 +24,9 @@
  * Readings taken where the paper is silent (each also listed in the design notes):
  *   R1  eta (re-orthogonalisation threshold) is not given: 1/sqrt(2) in conditional
  *       mode; the default mode re-orthogonalises always (one extra CGS pass).
- *   R2  Fig. 1 step 12's second clause is read as a breakdown test
+ *   R2  the second clause of Fig. 1's breakdown test is read as a breakdown test
  *       !(h_{j+1,j} > eps_bd * omega); literal_fig1 = 1 restores the printed clause.
- *   R3  the division v := w / h_{j+1,j} (Fig. 1 steps 1, 13) is a multiplication by the
+ *   R3  the division v := w / h_{j+1,j} (Fig. 1, first vector and basis extension) is a multiplication by the
  *       FP64 reciprocal 1/h, so that the stored codes are a fixed function of w.
  *   R4  "stored as v_j / sigma_j" (Section 4.2): q_i = clamp(rint(v_i / sigma_j)) with
  *       v = w / ||w||_2 normalised, sigma_j = max_i |v_i| / max_int (equal to the printed
@@ -38,7 +38,7 @@
  *       part of the definition; e4m3 saturates to +-448.
  *   R6  f16 is a single round-to-nearest-even of the FP64 value (no scale), as a plain
  *       IEEE cast (Section 4.2 lists float16 without scaling).
- *   R7  iterations = Arnoldi steps (sparse products of Fig. 1 step 3); maxit caps them.
+ *   R7  iterations = Arnoldi steps (sparse products of Fig. 1's Arnoldi step); maxit caps them.
  *   R8  ||b|| = 0 returns x = 0 (exact solution) with zero iterations.
  */
 #ifndef CBG_ORACLE_H
@@ -51,10 +51,10 @@ extern "C" {
 
 /* storage formats of the Krylov basis */
 enum { OR_F64 = 0, OR_F32 = 1, OR_F16 = 2, OR_BF16 = 3, OR_E4M3 = 4, OR_I32 = 5, OR_I16 = 6 };
-/* preconditioners (right preconditioning, Fig. 1 step 3 / step 17) */
+/* preconditioners (right preconditioning, Fig. 1) */
 enum { OR_PC_NONE = 0, OR_PC_JACOBI = 1, OR_PC_SPAI = 2,
        OR_PC_BJ4 = 3 /* block-Jacobi, blocks of 4 consecutive rows (Section 5.5) */ };
-/* re-orthogonalisation modes (Fig. 1 steps 7-11) */
+/* re-orthogonalisation modes (Fig. 1) */
 enum { OR_REORTH_ALWAYS = 0, OR_REORTH_CONDITIONAL = 1, OR_REORTH_NEVER = 2 };
 /* status codes */
 enum { OR_OK = 0, OR_NOT_CONVERGED = 1, OR_ERR_ARG = -1, OR_ERR_NONFINITE = -2 };
@@ -94,7 +94,7 @@ typedef struct {
     int32_t fmt;            /* OR_F64 ... OR_I16                                    */
     int32_t precond;        /* OR_PC_*                                              */
     int32_t reorth;         /* OR_REORTH_*                                          */
-    int32_t literal_fig1;   /* 1: Fig. 1 step 12 taken literally (reading R2)      */
+    int32_t literal_fig1;   /* 1: Fig. 1's breakdown clause literally (R2)       */
     int32_t adapt;          /* 1: adaptive basis format (reading R15)              */
     double  eta;            /* conditional re-orthogonalisation threshold          */
     double  eps_bd;         /* breakdown threshold on h_{j+1,j} / omega            */

@@ -1,4 +1,4 @@
-// cbg_kernels.cuh -- CUDA kernels of the restarted Arnoldi step (Fig. 1 steps 3-14),
+// cbg_kernels.cuh -- CUDA kernels of the restarted Arnoldi step (the Arnoldi step of Fig. 1),
 // templated on the basis storage format and on the arithmetic mode.
 //
 // Data layout in HBM (per solver handle):
@@ -31,7 +31,7 @@ struct DevState {
     long long reorths;
     double bnorm, target; // ||b||, tau ||b||
     double beta, rinf;    // ||r0||_2, ||r0||_inf of the current cycle
-    double omega;         // ||A z|| of the current step (Fig. 1 step 4)
+    double omega;         // ||A z|| of the current step (omega of Fig. 1)
     double eps_bd;        // breakdown threshold
     double est;           // |g_{j+1}|
     double hn;            // h_{j+1,j}
@@ -103,7 +103,7 @@ __device__ __forceinline__ double chunk_f64(const uint4& raw, const Chunk<FMT>& 
     }
 }
 
-// ============================================================== h = V^T w  (steps 5, 8)
+// ============================================================== h = V^T w  (CGS)
 // Row-per-lane schedule (the axpy's): a lane owns E consecutive rows (one 16-byte code
 // chunk per column) at a time, and the 32 lanes of a warp read 512 contiguous bytes of
 // each column.  Every warp runs through its segments once per group of CG columns, keeping one
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
     }
 }
 
-// ========================================== store v_{j+1} = w / h_{j+1,j} (steps 6, 12-14)
+// ========================================== store v_{j+1} = w / h_{j+1,j} (basis extension)
 // Every block reads the norms finalised by the preceding axpy, forms h_{j+1,j}, 1/h and
 // the format's scale, and encodes its rows into column `col`.  The last block to finish
 // additionally completes the Hessenberg column j (h from pass 1 plus u from pass 2),
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
 }
 
 // ======================================================= SpMV with on-the-fly decode
-// y = A x (x FP64) or y = A dec(code column) (Fig. 1 step 3; right preconditioning with
+// y = A x (x FP64) or y = A dec(code column) (the Arnoldi SpMV of Fig. 1; right preconditioning with
 // Jacobi is folded into the stored values A D^{-1}).  GROUP lanes per CSR row.  The
 // per-block sum of squares and max |y| of the owned rows go to part; in residual mode
 // y = b - A x.  The last block turns the partials into omega (Arnoldi mode) or beta /

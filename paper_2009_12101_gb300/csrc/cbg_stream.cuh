@@ -1,4 +1,4 @@
-// cbg_stream.cuh -- the basis dot product h = V^T w (Fig. 1 steps 5 and 8) with the
+// cbg_stream.cuh -- the basis dot product h = V^T w (the CGS projection and its re-orthogonalisation, Fig. 1) with the
 // compressed basis staged in shared memory by bulk copies (TMA).
 //
 // One block per SM: sixteen consumer warps and one producer warp.  A block owns a
@@ -131,7 +131,7 @@ __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes
     }
 }
 
-// ============================================================== h = V^T w  (steps 5, 8)
+// ============================================================== h = V^T w  (CGS)
 // Consumer warp of the dot: rows r .. r+E-1 of the tile and the CGW = CG/2 columns
 // starting at q0 within the stage, as packed pairs.  A missing column (>= nc) holds
 // stale codes; its lane of the pair is never read back (only columns < nc are kept).

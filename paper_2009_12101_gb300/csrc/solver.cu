@@ -1,17 +1,17 @@
 // solver.cu -- host driver of the restarted Arnoldi process and the C ABI (cbgmres.h).
 //
 // One restart cycle (Fig. 1):
-//   residual kernel     r = b - A x, beta = ||r||, ||r||_inf        (step 1 / step 18)
+//   residual kernel     r = b - A x, beta = ||r||, ||r||_inf        (cycle start / restart)
 //   cycle-start kernel  decides whether the cycle runs, g = beta e1
 //   store (mode 1)      v_1 = r / beta, compressed into V[:,0]
 //   per step j (all enqueued asynchronously, self-disabling once the cycle stops):
-//     spmv     w = A M^{-1} v_j  (decode fused), omega = ||w||       (steps 3-4)
-//     dot      h = V_j^T w                                           (step 5)
-//     axpy     w1 = w - V_j h                                        (step 5)
-//     dot      u = V_j^T w1                                          (step 8)
-//     axpy     w2 = w1 - V_j u, ||w2||_2, ||w2||_inf                 (steps 8-10)
-//     store    h_{j+1,j} = ||w2||, Givens update, v_{j+1} -> V        (steps 6, 12-14)
-//   backsolve y = R^{-1} g; x += M^{-1} (V y)                        (step 17)
+//     spmv     w = A M^{-1} v_j  (decode fused), omega = ||w||       (Arnoldi SpMV)
+//     dot      h = V_j^T w                                           (CGS)
+//     axpy     w1 = w - V_j h                                        (CGS)
+//     dot      u = V_j^T w1                                          (re-orth.)
+//     axpy     w2 = w1 - V_j u, ||w2||_2, ||w2||_inf                 (re-orth.)
+//     store    h_{j+1,j} = ||w2||, Givens update, v_{j+1} -> V        (extension)
+//   backsolve y = R^{-1} g; x += M^{-1} (V y)                        (LS update)
 // The host reads the explicit residual once per cycle and polls a mapped flag every
 // `check_every` steps to stop enqueueing once the device has ended the cycle.
 #include <cuda_runtime.h>
@@ -272,7 +272,7 @@ __global__ void k_cycle_start(DevArrays d, long long maxit, int m)
     d.g[0] = beta;
 }
 
-// y = R^{-1} g on the k x k upper triangle (Fig. 1 step 17); one warp, column-oriented:
+// y = R^{-1} g on the k x k upper triangle (the least-squares step of Fig. 1); one warp, column-oriented:
 // y_c = g_c / R_cc, then g_i -= R_ic y_c for i < c (lanes split i; column c is
 // contiguous).  The next column is prefetched while the current one is applied.
 __global__ void k_backsolve(DevArrays d)
@@ -543,7 +543,7 @@ void enqueue_step(cbg_handle* h, int j)
     const int* active = &h->d.st->active;
     const unsigned char* Vj = h->V + (long long)j * h->ldb;
     float* wdf = h->opt.arith == CBG_ARITH_DF32 ? reinterpret_cast<float*>(h->wdf) : nullptr;
-    // steps 3-4: w = A M^{-1} v_j, omega
+    // w = A M^{-1} v_j, omega
     {
         SpmvArgs a = spmv_args(h);
         a.active = active;
@@ -582,7 +582,7 @@ void enqueue_step(cbg_handle* h, int j)
     const int ncols = j + 1;
     const bool reorth = h->opt.reorth != CBG_REORTH_NEVER;
     const double pass_bytes = (double)ncols * (double)h->n * (double)fmt_bytes(h->fmt);
-    // step 5: h = V^T w ; w1 = w - V h
+    // CGS: h = V^T w ; w1 = w - V h
     DotArgs da{};
     da.V = h->V;
     da.ldb = h->ldb;
@@ -623,7 +623,7 @@ void enqueue_step(cbg_handle* h, int j)
     xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
     launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
     if (reorth) {
-        // step 8: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
+        // re-orthogonalisation: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
         da.w = h->w1;
         da.counter = h->d.counters + 3;
         da.out = h->d.u;
@@ -636,7 +636,7 @@ void enqueue_step(cbg_handle* h, int j)
         xa.counter = h->d.counters + 5;
         launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
     }
-    // steps 6, 12-14 and the Givens update
+    // h_{j+1,j}, breakdown test, basis extension and the Givens update
     StoreArgs sa{};
     sa.d = h->d;
     sa.w = h->w2;

@@ -1,5 +1,5 @@
 // spmv_f64.cu -- SpMV kernels with an FP64 input vector: explicit residual (Fig. 1
-// step 1), the second stage of A (P v), and the x update's x += P t.
+// the residual of Fig. 1), the second stage of A (P v), and the x update's x += P t.
 #include "cbg_launch_impl.cuh"
 namespace cbg {
 void spmv_f64(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a)

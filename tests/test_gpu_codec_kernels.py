@@ -1,5 +1,5 @@
 """GPU parity of the basis accessor (Section 4.2) and of the basis products
-(Fig. 1 steps 5 and 8) against the CPU oracle, through the C ABI."""
+(the CGS projection and re-orthogonalisation of Fig. 1) against the CPU oracle, through the C ABI."""
 import numpy as np
 import pytest
 

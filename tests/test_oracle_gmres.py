@@ -231,7 +231,7 @@ def test_reorth_modes(oracle_lib):
 
 
 def test_literal_fig1_clause_truncates_cycles(oracle_lib):
-    """Reading R2: the printed second clause of Fig. 1 step 12 ends a cycle as soon as
+    """Reading R2: the printed second clause of Fig. 1's breakdown test ends a cycle as soon as
     h_{j+1,j} < eta * omega; on this problem that happens within the first steps."""
     A = W.convdiff3d(8)
     b = W.rhs_sin(A.n)
