@@ -34,6 +34,7 @@ CODE_DTYPE = {F64: np.float64, F32: np.float32, F16: np.uint16, BF16: np.uint16,
               E4M3: np.uint8, I32: np.int32, I16: np.int16}
 PC_NONE, PC_JACOBI, PC_SPAI, PC_BJ4 = 0, 1, 2, 3
 REORTH_ALWAYS, REORTH_CONDITIONAL, REORTH_NEVER = 0, 1, 2
+ORTHO_CGS, ORTHO_MGS = 0, 1
 OK, NOT_CONVERGED, ERR_ARG, ERR_NONFINITE = 0, 1, -1, -2
 
 
@@ -62,6 +63,7 @@ class GmresArgs(C.Structure):
         ("true_relres", C.c_double), ("est_relres", C.c_double),
         ("status", C.c_int32), ("pad1", C.c_int32),
         ("adapt_gap", C.c_double), ("fmt_final", C.c_int32), ("promotions", C.c_int32),
+        ("ortho", C.c_int32), ("pad2", C.c_int32),
     ]
 
 
@@ -81,6 +83,7 @@ def lib():
             L.or_spmv.restype = None
             L.or_dot.argtypes = [i64, vp, vp]
             L.or_dot.restype = d
+            L.or_gram_schmidt_pass.argtypes = [i64, vp, i64, C.c_int, vp, vp]
             L.or_gmres.argtypes = [i64, vp, vp, vp, vp, vp, C.POINTER(GmresArgs)]
             L.or_mlp_forward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_spai_slots.argtypes = [i64, vp, vp, i64, i64, vp]
@@ -175,12 +178,25 @@ def dot(a, b):
     return lib().or_dot(a.size, _p(a), _p(b))
 
 
+def gram_schmidt_pass(V, w, ortho=ORTHO_CGS):
+    """One Gram-Schmidt pass of w against the columns of V (n x k): returns (coefficients,
+    reduced w); CGS as Fig. 1 prints it or the MGS variant."""
+    V = np.asarray(V, np.float64)
+    n, k = V.shape
+    Vc = np.asfortranarray(V)
+    w = np.array(w, dtype=np.float64, copy=True)
+    c = np.zeros(k)
+    lib().or_gram_schmidt_pass(n, Vc.ctypes.data, k, ortho, _p(w), _p(c))
+    return c, w
+
+
 # -------------------------------------------------------------------------------- GMRES
 def gmres(A, b, x0=None, *, m: int = 100, fmt: int = F64, precond: int = PC_NONE,
           pvals=None, reorth: int = REORTH_ALWAYS, eta: float = 2 ** -0.5,
           eps_bd: float = 2.0 ** -46, literal_fig1: bool = False, tol: float = 1e-10,
           maxit: int | None = None, want_H1: bool = False, want_V1: bool = False,
-          hist_cap: int = 0, tres_cap: int = 0, adapt: bool = False, adapt_gap: float = 4.0) -> dict:
+          hist_cap: int = 0, tres_cap: int = 0, adapt: bool = False, adapt_gap: float = 4.0,
+          ortho: int = ORTHO_CGS) -> dict:
     """Run the oracle's GMRES(m).  Returns a dict with x, status, iters, cycles, reorths,
     true_relres, est_relres and the optional H1 ((m+1) x m raw Hessenberg of the first
     cycle), V1 (decoded basis of the first cycle), hist, tres."""
@@ -193,6 +209,7 @@ def gmres(A, b, x0=None, *, m: int = 100, fmt: int = F64, precond: int = PC_NONE
     a.m, a.fmt, a.precond, a.reorth = m, fmt, precond, reorth
     a.literal_fig1 = int(literal_fig1)
     a.adapt, a.adapt_gap = int(adapt), adapt_gap
+    a.ortho = ortho
     a.eta, a.eps_bd, a.tol, a.maxit = eta, eps_bd, tol, maxit
     keep = []
     if pvals is not None:

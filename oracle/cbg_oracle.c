@@ -354,6 +354,28 @@ static int compress_column(int fmt, int64_t n, const double* w, double h, void* 
 
 /* Adaptive basis format (reading R15; the paper fixes one format per solve): the next
  * format up the ladder e4m3 -> bf16 -> f32 -> f64, f16 -> f32, i16 -> i32 -> f64, or -1. */
+/* One Gram-Schmidt pass of w against the columns 0..ncols-1 of V (n x ncols,
+ * column-major), the coefficients into c.  CGS (Fig. 1): every coefficient from the same
+ * w, then w -= V c.  MGS (the variant Section 2 mentions): column by column, the
+ * coefficient from the current w, which that column then reduces at once. */
+void or_gram_schmidt_pass(int64_t n, const double* V, int64_t ncols, int ortho, double* w, double* c)
+{
+    const int64_t j = ncols - 1;
+    if (ortho == OR_ORTHO_MGS) {
+        for (int64_t i = 0; i <= j; i++) {
+            const double* vi = V + (size_t)i * (size_t)n;
+            c[i] = or_dot(n, vi, w);
+            for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * c[i];
+        }
+        return;
+    }
+    for (int64_t i = 0; i <= j; i++) c[i] = or_dot(n, V + (size_t)i * (size_t)n, w);
+    for (int64_t i = 0; i <= j; i++) {
+        const double* vi = V + (size_t)i * (size_t)n;
+        for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * c[i];
+    }
+}
+
 static int wider_format(int f)
 {
     if (f == OR_E4M3) return OR_BF16;
@@ -479,23 +501,15 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             or_spmv(n, rowptr, col, val, z, w);
             /* omega = ||w|| */
             double omega = nrm2(n, w);
-            /* CGS: h_{1:j,j} = V_j^T w, w = w - V_j h */
-            for (int64_t i = 0; i <= j; i++) h[i] = or_dot(n, V + (size_t)i * (size_t)n, w);
-            for (int64_t i = 0; i <= j; i++) {
-                const double* vi = V + (size_t)i * (size_t)n;
-                for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * h[i];
-            }
+            /* Gram-Schmidt: h_{1:j,j} = V_j^T w, w = w - V_j h (CGS; or MGS) */
+            or_gram_schmidt_pass(n, V, j + 1, a->ortho, w, h);
             /* h_{j+1,j} = ||w|| */
             double hn = nrm2(n, w);
             /* re-orthogonalise (always, or when h_{j+1,j} < eta omega) */
             int do_re = a->reorth == OR_REORTH_ALWAYS ||
                         (a->reorth == OR_REORTH_CONDITIONAL && hn < a->eta * omega);
             if (do_re) {
-                for (int64_t i = 0; i <= j; i++) u[i] = or_dot(n, V + (size_t)i * (size_t)n, w);
-                for (int64_t i = 0; i <= j; i++) {
-                    const double* vi = V + (size_t)i * (size_t)n;
-                    for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * u[i];
-                }
+                or_gram_schmidt_pass(n, V, j + 1, a->ortho, w, u);
                 for (int64_t i = 0; i <= j; i++) h[i] += u[i];
                 hn = nrm2(n, w);
                 a->reorths++;

@@ -12,7 +12,8 @@
  *   - Fig. 1 (restarted, right-preconditioned GMRES(m) with classical Gram-Schmidt and
  *     optional re-orthogonalisation), step by step;
  *   - Section 2 (stopping test ||b - A x||_2 <= tau ||b||_2, QR/Givens update of the
- *     Hessenberg least-squares problem);
+ *     Hessenberg least-squares problem; the modified Gram-Schmidt variant it names as
+ *     the alternative to CGS, selected by or_gmres_args.ortho);
  *   - Section 3 ("CB-GMRES": basis stored in a compact format, all arithmetic FP64, the
  *     basis decompressed before each product with it in Fig. 1);
  *   - Section 4.2 (memory accessor; fixed-point formats with the per-vector scale
@@ -56,6 +57,10 @@ enum { OR_PC_NONE = 0, OR_PC_JACOBI = 1, OR_PC_SPAI = 2,
        OR_PC_BJ4 = 3 /* block-Jacobi, blocks of 4 consecutive rows (Section 5.5) */ };
 /* re-orthogonalisation modes (Fig. 1) */
 enum { OR_REORTH_ALWAYS = 0, OR_REORTH_CONDITIONAL = 1, OR_REORTH_NEVER = 2 };
+/* orthogonalisation: classical Gram-Schmidt as Fig. 1 prints it, or the modified
+ * Gram-Schmidt variant Section 2 mentions (each coefficient taken against w as already
+ * reduced by the columns before it) */
+enum { OR_ORTHO_CGS = 0, OR_ORTHO_MGS = 1 };
 /* status codes */
 enum { OR_OK = 0, OR_NOT_CONVERGED = 1, OR_ERR_ARG = -1, OR_ERR_NONFINITE = -2 };
 
@@ -86,6 +91,10 @@ int or_decode(int fmt, int64_t n, const void* codes, double scale, double* out);
 void   or_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                const double* x, double* y);              /* y = A x, row sums in CSR order */
 double or_dot(int64_t n, const double* a, const double* b); /* sequential sum           */
+/* one Gram-Schmidt pass of w against the ncols columns of V (n x ncols, column-major):
+ * coefficients c (ncols), w reduced in place; ortho = OR_ORTHO_CGS or OR_ORTHO_MGS */
+void   or_gram_schmidt_pass(int64_t n, const double* V, int64_t ncols, int ortho, double* w,
+                            double* c);
 
 /* ---- GMRES(m) (Fig. 1 with Section 5.2's explicit-residual recheck) --------------- */
 typedef struct {
@@ -115,6 +124,8 @@ typedef struct {
     double  adapt_gap;      /* promotion threshold of adapt                         */
     int32_t fmt_final;      /* out: basis format of the last cycle                  */
     int32_t promotions;     /* out: format promotions                               */
+    int32_t ortho;          /* OR_ORTHO_* (CGS by default)                          */
+    int32_t pad2;
 } or_gmres_args;
 
 int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,

@@ -396,3 +396,81 @@ def test_adapt_rescues_an_8_bit_basis():
     assert r1["promotions"] >= 1 and r1["iters"] < 0.8 * r0["iters"]
     assert r1["iters"] >= rf["iters"]
     assert r1["true_relres"] <= 1e-10
+
+
+# ------------------------------------------------ modified Gram-Schmidt variant (Section 2)
+def test_gram_schmidt_lauchli_closed_forms(oracle_lib):
+    """Lauchli's matrix [1 1 1; d 0 0; 0 d 0; 0 0 d] with d = 1e-8, so that 1 + d^2 rounds
+    to 1. Worked by hand in that arithmetic, q1 = (1, d, 0, 0) and q2 = (0, -1, 1, 0)/sqrt 2.
+    CGS then gives q3 = (0, -1, 0, 1)/sqrt 2, so q2.q3 = 1/2. MGS gives
+    q3 = (0, -1, -1, 2)/sqrt 6, so q2.q3 = 0. This is Bjorck's classic example. A pass
+    that took MGS's coefficients from the unreduced w would reproduce CGS and fail."""
+    d = 1e-8
+    a = np.zeros((4, 3)); a[0, :] = 1.0; a[1, 0] = a[2, 1] = a[3, 2] = d
+    q = {}
+    for name, ortho in (("cgs", O.ORTHO_CGS), ("mgs", O.ORTHO_MGS)):
+        Q = np.zeros((4, 3))
+        for k in range(3):
+            w = a[:, k].copy()
+            if k:
+                c, w = O.gram_schmidt_pass(Q[:, :k], w, ortho)
+                assert c[0] == 1.0                          # q1 . a_k = 1 exactly
+            Q[:, k] = w / np.linalg.norm(w)
+        q[name] = Q
+    assert np.allclose(q["cgs"][:, 1], np.array([0, -1, 1, 0]) / np.sqrt(2), rtol=0, atol=1e-15)
+    assert np.allclose(q["cgs"][:, 2], np.array([0, -1, 0, 1]) / np.sqrt(2), rtol=0, atol=1e-15)
+    assert abs(q["cgs"][:, 1] @ q["cgs"][:, 2] - 0.5) <= 1e-15
+    assert np.allclose(q["mgs"][:, 2], np.array([0, -1, -1, 2]) / np.sqrt(6), rtol=0, atol=1e-15)
+    assert abs(q["mgs"][:, 1] @ q["mgs"][:, 2]) <= 1e-15
+
+
+def test_gram_schmidt_pass_one_column_and_orthonormal_columns(oracle_lib):
+    """Against one column both variants are the same projection. Against orthonormal
+    columns they give the same coefficients, V^T w, to rounding."""
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(50); v /= np.linalg.norm(v)
+    w = rng.standard_normal(50)
+    for ortho in (O.ORTHO_CGS, O.ORTHO_MGS):
+        c, r = O.gram_schmidt_pass(v[:, None], w, ortho)
+        assert abs(c[0] - v @ w) <= 1e-14 * np.linalg.norm(w)
+        assert np.allclose(r, w - (v @ w) * v, rtol=0, atol=1e-14)
+    Qm, _ = np.linalg.qr(rng.standard_normal((50, 7)))
+    c1, r1 = O.gram_schmidt_pass(Qm, w, O.ORTHO_CGS)
+    c2, r2 = O.gram_schmidt_pass(Qm, w, O.ORTHO_MGS)
+    assert np.allclose(c1, Qm.T @ w, rtol=0, atol=1e-13)
+    assert np.allclose(c2, Qm.T @ w, rtol=0, atol=1e-13)
+    assert np.allclose(r1, r2, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("reorth", [O.REORTH_ALWAYS, O.REORTH_NEVER])
+def test_mgs_iterates_are_krylov_minimisers(oracle_lib, reorth):
+    """MGS builds the same Krylov space. Each iterate is still the dense least-squares
+    minimiser over it, and the Givens recurrence gives that minimiser's residual."""
+    n = 30
+    a = _rand_nonsym(n, 6, shift=2.0) + np.diag(np.linspace(0.5, 4, n))
+    A = W.from_dense(a)
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(n); x0 = rng.standard_normal(n) * 0.1
+    bn = np.linalg.norm(b)
+    for k in range(1, 9):
+        r = O.gmres(A, b, x0, m=20, tol=0.0, maxit=k, hist_cap=k, reorth=reorth, ortho=O.ORTHO_MGS)
+        xk, resk = _krylov_ls(a, np.eye(n), b, x0, k)
+        assert np.linalg.norm(r["x"] - xk) <= 1e-10 * np.linalg.norm(xk)
+        assert abs(r["hist"][k - 1] - resk / bn) <= 1e-12
+
+
+def test_mgs_arnoldi_relation_and_orthogonality(oracle_lib):
+    """A V_k = V_{k+1} H_k and V^T V = I hold for the MGS basis (f64 codes, one
+    re-orthogonalisation pass). Its Hessenberg matrix equals the CGS one to rounding."""
+    A = W.convdiff3d(8)
+    a = A.dense()
+    b = W.rhs_sin(A.n)
+    k = 40
+    rm = O.gmres(A, b, m=k, tol=0.0, maxit=k, want_H1=True, want_V1=True, ortho=O.ORTHO_MGS)
+    rc = O.gmres(A, b, m=k, tol=0.0, maxit=k, want_H1=True, ortho=O.ORTHO_CGS)
+    V, H = rm["V1"], rm["H1"][: k + 1, :k]
+    assert np.linalg.norm(a @ V[:, :k] - V @ H) <= 1e-13 * np.linalg.norm(a, 2) * np.sqrt(k)
+    assert np.linalg.norm(np.eye(k + 1) - V.T @ V, 2) <= 1e-13
+    for j in range(k):
+        hm, hc = rm["H1"][: j + 2, j], rc["H1"][: j + 2, j]
+        assert np.linalg.norm(hm - hc) <= 1e-12 * np.linalg.norm(hc), j
