@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
+    p.add_argument("--ortho", choices=["cgs", "mgs"], default="cgs",
+                   help="orthogonalisation of the single-system solver (Fig. 1's CGS, or MGS)")
     p.add_argument("--batch-nsys", type=int, default=512,
                    help="systems of the batch workload (512 is the benchmark; fewer for profiling)")
     p.add_argument("--schedule", type=int, nargs=2, metavar=("CLUSTER", "SPLIT_ROWS"),
@@ -586,7 +588,7 @@ def main():
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, precond=args.precond,
-                                     adapt=args.adapt, profile=True)
+                                     adapt=args.adapt, ortho=args.ortho, profile=True)
                for f in fmts}
 
     def solve_all(record):
@@ -694,8 +696,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "df32" if args.arith == "df32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + ("" if args.precond == "none" else f"_{args.precond}")
-                                   + ("_adaptive" if args.adapt else ""),
+                                   + ("_adaptive" if args.adapt else "") + ("_mgs" if args.ortho == "mgs" else ""),
                        "n": n, "nnz": A.nnz, "restart": args.restart, "precond": args.precond,
+                       "orthogonalisation": args.ortho,
                        "adaptive_format": bool(args.adapt),
                        "tol": args.tol, "headline_format": args.headline, "formats": fmts,
                        "arith": ("basis products and the per-step SpMV in double-float (FP32 pairs); "

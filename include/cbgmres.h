@@ -52,6 +52,14 @@ typedef enum {
 typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2, CBG_PC_BJ4 = 3 } cbg_precond;
 typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
 
+/* Orthogonalisation (Fig. 1 prints classical Gram-Schmidt; Section 2 names modified
+ * Gram-Schmidt as the alternative and prefers CGS for its BLAS-2 efficiency).
+ * CBG_ORTHO_CGS: one basis dot and one basis axpy per pass over all j+1 columns (default).
+ * CBG_ORTHO_MGS: column by column, each coefficient from w as the previous columns have
+ *   reduced it: 2(j+1) dependent one-column launches per pass.  Same passes (reorth),
+ *   arithmetic and Hessenberg output.  Single-system solver only. */
+typedef enum { CBG_ORTHO_CGS = 0, CBG_ORTHO_MGS = 1 } cbg_ortho;
+
 /* Arithmetic of the basis products (the CGS projection, its re-orthogonalisation and
  * the solution update of Fig. 1) and of the per-step SpMV.
  * CBG_ARITH_DF32: products and partial sums in double-float (pairs of FP32 with
@@ -122,6 +130,8 @@ typedef struct {
                                 basis is then allocated for 8-byte codes.  Default 0.      */
     int32_t pad1;
     double adapt_gap;        /* promotion threshold of adapt (default 4)                */
+    int32_t ortho;           /* cbg_ortho, default CBG_ORTHO_CGS                        */
+    int32_t pad2;
 } cbg_options;
 
 typedef struct {
@@ -219,7 +229,7 @@ int cbg_encode(int fmt, int64_t n, const double* v, double vmax, void* codes,
 int cbg_decode(int fmt, int64_t n, const void* codes, double scale, double* out,
                void* stream);
 
-/* ---- basis products, exposed for parity checks (CGS and re-orthogonalisation, Fig. 1) -------------
+/* ---- basis products, exposed for parity checks (CGS and re-orthogonalisation, Fig. 1) ---
  * V: device codes, ncols columns of leading dimension ld elements; scales[ncols] host.
  * cbg_basis_dot:  h[k] = sum_i dec(V[i,k]) w[i]      (h: host, w: device)
  * cbg_basis_axpy: w[i] -= sum_k dec(V[i,k]) h[k]     (h: host, w: device, in place)
@@ -285,7 +295,7 @@ int cbgmres_spmv(cbg_handle* h, const double* x, double* y);
 /* ---- batched solve (many independent systems, one persistent launch) ---------------
  * nsys systems As[s] (host or device CSR per on_device), all with restart length
  * `restart` (<= 64) and basis format `fmt`; options.precond NONE or JACOBI, reorth ALWAYS,
- * arith DF32.  One persistent kernel with thread-block clusters runs every GMRES(m)
+ * arith DF32, ortho CGS.  One persistent kernel with thread-block clusters runs every GMRES(m)
  * solve on the device (Fig. 1 with the explicit-residual recheck of Section 5.2): a
  * device work queue hands out systems in decreasing size; systems with at least
  * `split_rows` rows are solved by a whole cluster (rows split across its blocks, sums

@@ -26,6 +26,7 @@ FORMAT_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e4m3": 1, "i32": 4, "i
 PRECONDS = {"none": 0, "jacobi": 1, "spai": 2, "bj4": 3}
 REORTH = {"always": 0, "conditional": 1, "never": 2}
 ARITH = {"df32": 0, "fp64": 1}
+ORTHO = {"cgs": 0, "mgs": 1}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "STAGNATED", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM",
           -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_UNSUPPORTED"}
 TILE_ROWS = 4096   # padded rows per basis column (multiple of every kernel tile)
@@ -50,7 +51,7 @@ class Options(C.Structure):
                 ("spmv_group", C.c_int32), ("eta", C.c_double), ("breakdown_eps", C.c_double),
                 ("stream", C.c_void_p), ("check_every", C.c_int32), ("use_graph", C.c_int32),
                 ("profile", C.c_int32), ("stop_on_stagnation", C.c_int32), ("adapt", C.c_int32),
-                ("pad1", C.c_int32), ("adapt_gap", C.c_double)]
+                ("pad1", C.c_int32), ("adapt_gap", C.c_double), ("ortho", C.c_int32), ("pad2", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -167,12 +168,13 @@ def _dev_f64(t, n=None, name="vector"):
 
 def options(precond="none", arith="df32", reorth="always", spmv_group=0, stream=None,
             check_every=4, eta=None, breakdown_eps=None, profile=False,
-            stop_on_stagnation=False, adapt=False, adapt_gap=None) -> Options:
+            stop_on_stagnation=False, adapt=False, adapt_gap=None, ortho="cgs") -> Options:
     o = Options()
     lib().cbgmres_options_default(C.byref(o))
     o.precond = PRECONDS[precond]
     o.arith = ARITH[arith]
     o.reorth = REORTH[reorth]
+    o.ortho = ORTHO[ortho]
     o.spmv_group = spmv_group
     o.check_every = check_every
     o.profile = int(bool(profile))
@@ -206,7 +208,8 @@ class Solver:
     def __init__(self, rowptr, col, val, *, restart: int = 100, fmt: str = "f64",
                  precond: str = "none", arith: str = "df32", reorth: str = "always",
                  spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False,
-                 stop_on_stagnation: bool = False, adapt: bool = False, adapt_gap: float | None = None):
+                 stop_on_stagnation: bool = False, adapt: bool = False, adapt_gap: float | None = None,
+                 ortho: str = "cgs"):
         torch = _torch()
         L = lib()
         self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
@@ -224,7 +227,8 @@ class Solver:
         self.ld = (self.n + TILE_ROWS - 1) // TILE_ROWS * TILE_ROWS
         opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
                       stream=stream, check_every=check_every, profile=profile,
-                      stop_on_stagnation=stop_on_stagnation, adapt=adapt, adapt_gap=adapt_gap)
+                      stop_on_stagnation=stop_on_stagnation, adapt=adapt, adapt_gap=adapt_gap,
+                      ortho=ortho)
         h = C.c_void_p()
         _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
                "cbgmres_create")

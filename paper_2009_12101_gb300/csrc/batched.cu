@@ -306,7 +306,8 @@ int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt, co
     if (opt) o = *opt;
     else cbgmres_options_default(&o);
     if (o.precond != CBG_PC_NONE && o.precond != CBG_PC_JACOBI) return CBG_ERR_UNSUPPORTED;
-    if (o.reorth != CBG_REORTH_ALWAYS || o.arith != CBG_ARITH_DF32) return CBG_ERR_UNSUPPORTED;
+    if (o.reorth != CBG_REORTH_ALWAYS || o.arith != CBG_ARITH_DF32 || o.ortho != CBG_ORTHO_CGS)
+        return CBG_ERR_UNSUPPORTED;
     cbg_batch* bt = new (std::nothrow) cbg_batch();
     if (!bt) return CBG_ERR_OOM;
     bt->nsys = nsys;

@@ -536,6 +536,47 @@ void enqueue_residual(cbg_handle* h, const double* b, const double* x)
     launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_RESIDUAL, h->group, h->grid_spmv, h->stream, a); });
 }
 
+// The modified Gram-Schmidt variant Section 2 names in place of CGS: within a pass,
+// column i's coefficient comes from w as columns 0..i-1 have already reduced it, and
+// w -= h_i v_i follows at once.  That is 2(j+1) dependent launches per pass (one-column
+// dot, one-column axpy) where CGS takes 2, each re-reading and re-writing w: the paper's
+// reason to prefer CGS.  DF32 keeps w as its double-float planes, reduced in place; FP64
+// alternates w between two buffers.  The final axpy writes w2 and finalises its norms
+// for the store kernel, like the CGS path.
+template <class Dot, class Axpy>
+void enqueue_mgs(cbg_handle* h, int j, bool reorth, float* wdf, DotArgs& da, AxpyArgs& xa, Dot&& run_dot,
+                 Axpy&& run_axpy)
+{
+    const int passes = reorth ? 2 : 1;
+    const double col_bytes = (double)h->n * (double)fmt_bytes(h->fmt);
+    double* cur = h->w;                       // FP64 arithmetic: the current w
+    for (int pass = 0; pass < passes; pass++) {
+        double* coef = pass == 0 ? h->d.h : h->d.u;
+        da.counter = h->d.counters + (pass == 0 ? 2 : 3);
+        for (int i = 0; i <= j; i++) {
+            const bool last = pass == passes - 1 && i == j;
+            da.V = h->V + (long long)i * h->ldb;
+            da.ncols = 1;
+            da.scales = h->d.scales + i;
+            da.w = cur;
+            da.out = coef + i;
+            launch(h, 0, col_bytes, run_dot);
+            xa.V = da.V;
+            xa.ncols = 1;
+            xa.scales = da.scales;
+            xa.coef = coef + i;
+            double* next = last ? h->w2 : (cur == h->w1 ? h->w : h->w1);
+            xa.w_in = wdf ? nullptr : cur;
+            xa.wdf_in = wdf;
+            xa.wdf_out = last ? nullptr : wdf;
+            xa.w_out = next;
+            xa.counter = last ? h->d.counters + 5 : nullptr;
+            launch(h, 1, col_bytes, [&] { run_axpy(xa); });
+            cur = next;
+        }
+    }
+}
+
 void enqueue_step(cbg_handle* h, int j)
 {
     const Ops& op = ops_for(h->fmt);
@@ -601,8 +642,6 @@ void enqueue_step(cbg_handle* h, int j)
         else op.dot(h->opt.arith, h->grid_dot, s, da);
     };
     auto run_axpy = [&](const AxpyArgs& xa) { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); };
-    launch(h, 0, pass_bytes, run_dot);
-
     AxpyArgs xa{};
     xa.V = h->V;
     xa.ldb = h->ldb;
@@ -613,12 +652,16 @@ void enqueue_step(cbg_handle* h, int j)
     xa.n = h->n;
     xa.part_norm = h->d.part_norm;
     xa.active = active;
+    xa.st = h->d.st;                                      // the final pass writes ||w||, max |w| here
+    if (h->opt.ortho == CBG_ORTHO_MGS) {
+        enqueue_mgs(h, j, reorth, wdf, da, xa, run_dot, run_axpy);
+    } else {
+    launch(h, 0, pass_bytes, run_dot);
     xa.coef = h->d.h;
     // DF32: the SpMV delivered w only as its double-float planes
     xa.w_in = wdf ? nullptr : h->w;
     xa.wdf_in = wdf;
     xa.w_out = reorth ? h->w1 : h->w2;
-    xa.st = h->d.st;
     xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
     xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
     launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
@@ -635,6 +678,7 @@ void enqueue_step(cbg_handle* h, int j)
         xa.wdf_out = nullptr;
         xa.counter = h->d.counters + 5;
         launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
+    }
     }
     // h_{j+1,j}, breakdown test, basis extension and the Givens update
     StoreArgs sa{};
@@ -898,6 +942,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     if (o.precond < CBG_PC_NONE || o.precond > CBG_PC_BJ4) return CBG_ERR_ARG;
     if (o.reorth == CBG_REORTH_CONDITIONAL) return CBG_ERR_UNSUPPORTED;
     if (o.reorth < CBG_REORTH_ALWAYS || o.reorth > CBG_REORTH_NEVER) return CBG_ERR_ARG;
+    if (o.ortho != CBG_ORTHO_CGS && o.ortho != CBG_ORTHO_MGS) return CBG_ERR_ARG;
     if (o.spmv_group != 0 && (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
         return CBG_ERR_ARG;
 

@@ -42,10 +42,22 @@ def test_status_strings_and_defaults(libcb):
     assert libcb.cbgmres_status_string(12345) == b"unknown status"
     o = cb.Options()
     libcb.cbgmres_options_default(C.byref(o))
-    assert o.reorth == 0 and o.precond == 0 and o.arith == 0 and o.check_every == 4
+    assert o.reorth == 0 and o.precond == 0 and o.arith == 0 and o.check_every == 4 and o.ortho == 0
     assert abs(o.eta - 2 ** -0.5) < 1e-15 and o.breakdown_eps == 2.0 ** -46
     assert [libcb.cbgmres_format_bytes(f) for f in range(7)] == [8, 4, 2, 2, 1, 4, 2]
     assert libcb.cbgmres_format_bytes(9) == 0
+
+
+def test_options_struct_size_matches_the_binding(libcb):
+    """cbgmres_options_default clears the whole C struct: on a buffer filled with a
+    pattern it must write exactly the binding's sizeof(Options) bytes (the trailing
+    fields default to zero), no fewer and no more."""
+    import paper_2009_12101_gb300 as cb
+    size = C.sizeof(cb.Options)
+    buf = (C.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    libcb.cbgmres_options_default(C.cast(buf, C.POINTER(cb.Options)))
+    assert all(b == 0xAB for b in buf[size:])
+    assert all(b == 0 for b in buf[size - 8:size])
 
 
 def test_argument_errors_need_no_gpu(libcb):
@@ -59,3 +71,20 @@ def test_argument_errors_need_no_gpu(libcb):
     scale = C.c_double()
     assert libcb.cbg_encode(17, 4, None, 1.0, None, C.byref(scale), None) == -1
     assert libcb.cbg_decode(0, -1, None, 1.0, None, None) == -1
+
+
+def test_ortho_option_is_checked_before_the_device(libcb):
+    """An unknown orthogonalisation is an argument error, and the batched solver (CGS
+    only) reports MGS as unsupported. Both are decided before any device call."""
+    import numpy as np
+    import paper_2009_12101_gb300 as cb
+    rp = np.array([0, 1, 2], np.int32); ci = np.array([0, 1], np.int32); va = np.array([2.0, 3.0])
+    csr = cb.Csr(2, 2, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, 0)
+    o = cb.Options()
+    libcb.cbgmres_options_default(C.byref(o))
+    o.ortho = 7
+    h = C.c_void_p()
+    assert libcb.cbgmres_create(C.byref(csr), 10, 0, C.byref(o), C.byref(h)) == -1
+    o.ortho = cb.ORTHO["mgs"]
+    bt = C.c_void_p()
+    assert libcb.cbgmres_create_batched(1, C.byref(csr), 10, 1, C.byref(o), C.byref(bt)) == -6
