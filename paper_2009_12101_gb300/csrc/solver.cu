@@ -656,29 +656,29 @@ void enqueue_step(cbg_handle* h, int j)
     if (h->opt.ortho == CBG_ORTHO_MGS) {
         enqueue_mgs(h, j, reorth, wdf, da, xa, run_dot, run_axpy);
     } else {
-    launch(h, 0, pass_bytes, run_dot);
-    xa.coef = h->d.h;
-    // DF32: the SpMV delivered w only as its double-float planes
-    xa.w_in = wdf ? nullptr : h->w;
-    xa.wdf_in = wdf;
-    xa.w_out = reorth ? h->w1 : h->w2;
-    xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
-    xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
-    launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
-    if (reorth) {
-        // re-orthogonalisation: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
-        da.w = h->w1;
-        da.counter = h->d.counters + 3;
-        da.out = h->d.u;
         launch(h, 0, pass_bytes, run_dot);
-        xa.coef = h->d.u;
-        xa.w_in = h->w1;
-        xa.wdf_in = nullptr;
-        xa.w_out = h->w2;
-        xa.wdf_out = nullptr;
-        xa.counter = h->d.counters + 5;
+        xa.coef = h->d.h;
+        // DF32: the SpMV delivered w only as its double-float planes
+        xa.w_in = wdf ? nullptr : h->w;
+        xa.wdf_in = wdf;
+        xa.w_out = reorth ? h->w1 : h->w2;
+        xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
+        xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
         launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
-    }
+        if (reorth) {
+            // re-orthogonalisation: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
+            da.w = h->w1;
+            da.counter = h->d.counters + 3;
+            da.out = h->d.u;
+            launch(h, 0, pass_bytes, run_dot);
+            xa.coef = h->d.u;
+            xa.w_in = h->w1;
+            xa.wdf_in = nullptr;
+            xa.w_out = h->w2;
+            xa.wdf_out = nullptr;
+            xa.counter = h->d.counters + 5;
+            launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
+        }
     }
     // h_{j+1,j}, breakdown test, basis extension and the Givens update
     StoreArgs sa{};
