@@ -50,6 +50,13 @@ typedef enum {
  *         block size 4); applied as z = D^{-1} v before the SpMV.  A singular block makes
  *         cbgmres_create fail with CBG_ERR_ARG. */
 typedef enum { CBG_PC_NONE = 0, CBG_PC_JACOBI = 1, CBG_PC_SPAI = 2, CBG_PC_BJ4 = 3 } cbg_precond;
+/* Re-orthogonalisation (Fig. 1's second Gram-Schmidt pass).
+ * ALWAYS (default): every step runs both passes (CGS2).
+ * CONDITIONAL: as Fig. 1 prints it, the second pass runs only when the first left
+ *   ||w|| < eta * omega (omega = ||A M^{-1} v_j||).  The decision is taken on the device
+ *   by the first pass's last block; the second pass's kernels skip themselves otherwise.
+ *   eta in (0, 1] (else CBG_ERR_ARG); CGS only (with MGS: CBG_ERR_UNSUPPORTED).
+ * NEVER: one pass. */
 typedef enum { CBG_REORTH_ALWAYS = 0, CBG_REORTH_CONDITIONAL = 1, CBG_REORTH_NEVER = 2 } cbg_reorth;
 
 /* Orthogonalisation (Fig. 1 prints classical Gram-Schmidt; Section 2 names modified

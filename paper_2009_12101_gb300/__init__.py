@@ -209,7 +209,7 @@ class Solver:
                  precond: str = "none", arith: str = "df32", reorth: str = "always",
                  spmv_group: int = 0, stream=None, check_every: int = 4, profile: bool = False,
                  stop_on_stagnation: bool = False, adapt: bool = False, adapt_gap: float | None = None,
-                 ortho: str = "cgs"):
+                 ortho: str = "cgs", eta: float | None = None):
         torch = _torch()
         L = lib()
         self.fmt, self.restart, self.precond, self.arith = fmt, restart, precond, arith
@@ -228,7 +228,7 @@ class Solver:
         opt = options(precond=precond, arith=arith, reorth=reorth, spmv_group=spmv_group,
                       stream=stream, check_every=check_every, profile=profile,
                       stop_on_stagnation=stop_on_stagnation, adapt=adapt, adapt_gap=adapt_gap,
-                      ortho=ortho)
+                      ortho=ortho, eta=eta)
         h = C.c_void_p()
         _check(L.cbgmres_create(C.byref(csr), restart, FORMATS[fmt], C.byref(opt), C.byref(h)),
                "cbgmres_create")

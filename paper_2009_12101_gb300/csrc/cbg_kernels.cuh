@@ -39,6 +39,9 @@ struct DevState {
     int last_k;           // columns of the previous cycle (set when a cycle starts)
     int fault;            // nonzero: a pipelined kernel gave up waiting (FAULT_TIMEOUT)
     double wnorm, wmax;   // ||w||_2 and ||w||_inf of the orthogonalised w (last axpy block)
+    int reorth_now;       // conditional mode: the current step's second pass runs (set by the
+                          // first pass's last axpy block, cleared by the store's finalize)
+    int pad_state;
 };
 
 // per-handle arrays addressed by the kernels
@@ -397,6 +400,8 @@ struct AxpyArgs {
     DevState* st;
     float* wdf_out;           // EPI_SUB: also store w_out split, planar hi[nrows] then lo[nrows] (may be null)
     const float* wdf_in;      // EPI_SUB, DF32: w_in given as such planes instead (may be null; may equal wdf_out)
+    int* reorth_flag;         // EPI_SUB with counter, conditional re-orthogonalisation (Fig. 1): the
+    double eta;               //   last block sets *reorth_flag = (||w_out|| < eta * st->omega)
 };
 
 // Blocks per SM asked of the register allocator: 4 for 8-byte codes (measured 5 % faster
@@ -574,8 +579,10 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                 double s2, m2;
                 reduce_norm_parts(a.part_norm, gridDim.x, s2, m2);
                 if (threadIdx.x == 0) {
-                    a.st->wnorm = sqrt(s2);
+                    const double wn = sqrt(s2);
+                    a.st->wnorm = wn;
                     a.st->wmax = m2;
+                    if (a.reorth_flag) *a.reorth_flag = wn < a.eta * a.st->omega ? 1 : 0;
                 }
             }
         }
@@ -603,6 +610,8 @@ struct StoreArgs {
     unsigned int* counter;    // last-block counter (mode 0: the last block runs the finalize)
     int hexp;                 // mode 0: the column (h, ||w||) came from the operator scaled by
                               // 2^-hexp; the Hessenberg column is it times 2^hexp (0: as is)
+    const int* reorth_dev;    // conditional mode: device flag replacing `reorth`; when it is 0
+    const double* w_alt;      //   the vector to store is w_alt (the first pass's output)
 };
 
 
@@ -622,6 +631,7 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     DevState* st = a.d.st;
     const int j = a.j, ldh = st->m + 1;
     const int lane = threadIdx.x & 31;
+    const int reorth = a.reorth_dev ? *a.reorth_dev : a.reorth;   // did the second pass run
     // back from the power-of-two normalised operator (exact)
     const double hs = a.hexp ? pow2d(a.hexp) : 1.0;
     hn = __dmul_rn(hn, hs);
@@ -630,7 +640,7 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         double hv = 0.0;
         if (i <= j) {
             hv = __ldcg(a.d.h + i);
-            if (a.reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
+            if (reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
             hv = __dmul_rn(hv, hs);
         } else {
             hv = hn;
@@ -693,7 +703,8 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         st->hn = hn;
         st->k = j + 1;
         st->iters += 1;
-        if (a.reorth) st->reorths += 1;
+        if (reorth) st->reorths += 1;
+        st->reorth_now = 0;          // (every block of this store has read it already)
         if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
         int stop = 0;
         if (!isfinite(hn) || !isfinite(omega) || !isfinite(est)) stop = 3;
@@ -733,13 +744,14 @@ __global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
     const double inv = sh_inv;
     const EncParams ep = sh_ep;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
+    const double* wsrc = (a.reorth_dev && *a.reorth_dev == 0) ? a.w_alt : a.w;
     const long long stride = (long long)gridDim.x * THREADS;
     for (long long i0 = (long long)blockIdx.x * THREADS + threadIdx.x; i0 < a.n; i0 += 4 * stride) {
         double wv[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {   // four loads in flight per thread
             const long long i = i0 + q * stride;
-            wv[q] = i < a.n ? __ldcg(a.w + i) : 0.0;
+            wv[q] = i < a.n ? __ldcg(wsrc + i) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < 4; q++) {

@@ -251,6 +251,7 @@ __global__ void k_init_state(DevState* st, double bnorm, double target, double e
     st->hist_cap = hist_cap;
     st->last_k = 0;
     st->fault = 0;
+    st->reorth_now = 0;
 }
 
 // ================================================ cycle start / end (single block)
@@ -622,6 +623,7 @@ void enqueue_step(cbg_handle* h, int j)
     }
     const int ncols = j + 1;
     const bool reorth = h->opt.reorth != CBG_REORTH_NEVER;
+    const bool cond = h->opt.reorth == CBG_REORTH_CONDITIONAL;   // Fig. 1: when ||w1|| < eta omega
     const double pass_bytes = (double)ncols * (double)h->n * (double)fmt_bytes(h->fmt);
     // CGS: h = V^T w ; w1 = w - V h
     DotArgs da{};
@@ -662,14 +664,23 @@ void enqueue_step(cbg_handle* h, int j)
         xa.w_in = wdf ? nullptr : h->w;
         xa.wdf_in = wdf;
         xa.w_out = reorth ? h->w1 : h->w2;
-        xa.counter = reorth ? nullptr : h->d.counters + 5;   // the final pass finalises the norms
+        // the final pass finalises the norms; in conditional mode the first pass does too,
+        // and its last block decides on the device whether the second pass runs
+        xa.counter = reorth && !cond ? nullptr : h->d.counters + 5;
         xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
+        if (cond) {
+            xa.reorth_flag = &h->d.st->reorth_now;
+            xa.eta = h->opt.eta;
+        }
         launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
         if (reorth) {
-            // re-orthogonalisation: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel)
+            // re-orthogonalisation: u = V^T w1 ; w2 = w1 - V u ; (h += u in the store kernel);
+            // conditional mode: both kernels skip themselves unless the flag is set
+            const int* gate = cond ? &h->d.st->reorth_now : active;
             da.w = h->w1;
             da.counter = h->d.counters + 3;
             da.out = h->d.u;
+            da.active = gate;
             launch(h, 0, pass_bytes, run_dot);
             xa.coef = h->d.u;
             xa.w_in = h->w1;
@@ -677,6 +688,8 @@ void enqueue_step(cbg_handle* h, int j)
             xa.w_out = h->w2;
             xa.wdf_out = nullptr;
             xa.counter = h->d.counters + 5;
+            xa.reorth_flag = nullptr;
+            xa.active = gate;
             launch(h, 1, pass_bytes, [&] { run_axpy(xa); });
         }
     }
@@ -693,6 +706,10 @@ void enqueue_step(cbg_handle* h, int j)
     sa.fmt = h->fmt;
     sa.counter = h->d.counters + 6;
     sa.hexp = -h->pexp;
+    if (cond) {
+        sa.reorth_dev = &h->d.st->reorth_now;
+        sa.w_alt = h->w1;
+    }
     launch(h, 3, store_bytes(h), [&] { op.store(h->grid_store, s, sa); });
 }
 
@@ -940,9 +957,10 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     else cbgmres_options_default(&o);
     if (o.arith != CBG_ARITH_DF32 && o.arith != CBG_ARITH_FP64) return CBG_ERR_ARG;
     if (o.precond < CBG_PC_NONE || o.precond > CBG_PC_BJ4) return CBG_ERR_ARG;
-    if (o.reorth == CBG_REORTH_CONDITIONAL) return CBG_ERR_UNSUPPORTED;
     if (o.reorth < CBG_REORTH_ALWAYS || o.reorth > CBG_REORTH_NEVER) return CBG_ERR_ARG;
     if (o.ortho != CBG_ORTHO_CGS && o.ortho != CBG_ORTHO_MGS) return CBG_ERR_ARG;
+    if (o.reorth == CBG_REORTH_CONDITIONAL && o.ortho == CBG_ORTHO_MGS) return CBG_ERR_UNSUPPORTED;
+    if (o.reorth == CBG_REORTH_CONDITIONAL && !(o.eta > 0.0 && o.eta <= 1.0)) return CBG_ERR_ARG;
     if (o.spmv_group != 0 && (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
         return CBG_ERR_ARG;
 

@@ -74,8 +74,10 @@ def test_argument_errors_need_no_gpu(libcb):
 
 
 def test_ortho_option_is_checked_before_the_device(libcb):
-    """An unknown orthogonalisation is an argument error, and the batched solver (CGS
-    only) reports MGS as unsupported. Both are decided before any device call."""
+    """An unknown orthogonalisation is an argument error; the batched solver (CGS only)
+    reports MGS as unsupported, and so does the single-system solver for MGS with
+    conditional re-orthogonalisation; eta outside (0, 1] is an argument error there. All
+    are decided before any device call."""
     import numpy as np
     import paper_2009_12101_gb300 as cb
     rp = np.array([0, 1, 2], np.int32); ci = np.array([0, 1], np.int32); va = np.array([2.0, 3.0])
@@ -88,3 +90,10 @@ def test_ortho_option_is_checked_before_the_device(libcb):
     o.ortho = cb.ORTHO["mgs"]
     bt = C.c_void_p()
     assert libcb.cbgmres_create_batched(1, C.byref(csr), 10, 1, C.byref(o), C.byref(bt)) == -6
+    # conditional re-orthogonalisation: CGS only, eta in (0, 1]
+    o.reorth = cb.REORTH["conditional"]
+    assert libcb.cbgmres_create(C.byref(csr), 10, 0, C.byref(o), C.byref(h)) == -6
+    o.ortho = cb.ORTHO["cgs"]
+    for bad_eta in (0.0, -0.5, 1.5, float("nan")):
+        o.eta = bad_eta
+        assert libcb.cbgmres_create(C.byref(csr), 10, 0, C.byref(o), C.byref(h)) == -1

@@ -40,6 +40,37 @@ def test_hessenberg_first_columns(prob, fmt, arith):
     assert np.all(err <= 1e-10), err
 
 
+@pytest.mark.parametrize("eta", [0.3, 2 ** -0.5])
+@pytest.mark.parametrize("fmt", ["f64", "f32"])
+def test_conditional_reorth_parity(fmt, eta):
+    """Fig. 1's conditional re-orthogonalisation (second pass only when ||w1|| < eta omega),
+    decided on the device: the first 10 Hessenberg columns, then the full solve (same
+    number of second passes as the oracle, iterations within 2 %, x within 1e-6).  On this
+    problem ||w1|| / omega stays between 0.3 and 0.5, so eta = 0.3 skips nearly every
+    second pass and 1/sqrt 2 runs every one."""
+    torch, cb = need_gpu()
+    A, xs, b = _problem("convdiff20")
+    k = 10
+    r1 = O.gmres(A, b, m=20, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True,
+                 reorth=O.REORTH_CONDITIONAL, eta=eta)
+    with cb.Solver.from_csr(A, restart=20, fmt=fmt, reorth="conditional", eta=eta) as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+    err = col_relerr(Hg, r1["H1"], k)
+    assert np.all(err <= 1e-10), err
+    m, tol = 100, 1e-10
+    ro = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=tol, maxit=20000, reorth=O.REORTH_CONDITIONAL, eta=eta)
+    assert ro["status"] == O.OK
+    xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with cb.Solver.from_csr(A, restart=m, fmt=fmt, reorth="conditional", eta=eta) as s:
+        st = s.solve(to_dev(torch, b), xg, tol=tol, maxit=20000)
+    assert st["status"] == 0, st
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(b - O.spmv(A, x)) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    assert st["reorths"] == ro["reorths"], (st["reorths"], ro["reorths"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
 @pytest.mark.parametrize("arith", ["df32", "fp64"])
 @pytest.mark.parametrize("fmt,reorth", [("f64", "always"), ("f32", "always"), ("f16", "always"),
                                         ("i16", "always"), ("f64", "never"), ("f32", "never")])
