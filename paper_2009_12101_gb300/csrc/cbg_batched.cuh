@@ -308,8 +308,9 @@ template <int FMT> struct BatchedSolver {
         __syncthreads();
     }
 
-    // ws -= V coef over own rows; returns the thread's sum of squares and max |w| of the
-    // result (FP64 from the DF value).
+    // ws -= V coef over own rows; with NORMS, also the thread's sum of squares and max |w|
+    // of the result (FP64 from the DF value; only the last pass of a step needs them).
+    template <bool NORMS>
     static __device__ void axpy(const BatchArgs& a, const BatchSys& s, BtSmem* sm, int r0, int r1, int ncols,
                                 const double* coef, double& ss, double& mx)
     {
@@ -358,11 +359,13 @@ template <int FMT> struct BatchedSolver {
                 if (e0 + e < nloc) {
                     df_renorm(S[e], C[e]);
                     sm->ws[e0 + e] = make_float2(S[e], C[e]);
-                    const double d = df_to_double(S[e], C[e]);
-                    ss = __fma_rn(d, d, ss);
-                    // max |d| through the bit pattern (integer compare of non-negative doubles)
-                    const long long ab = __double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFll;
-                    mx = ab > __double_as_longlong(mx) ? __longlong_as_double(ab) : mx;
+                    if constexpr (NORMS) {
+                        const double d = df_to_double(S[e], C[e]);
+                        ss = __fma_rn(d, d, ss);
+                        // max |d| through the bit pattern (integer compare of non-negative doubles)
+                        const long long ab = __double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFll;
+                        mx = ab > __double_as_longlong(mx) ? __longlong_as_double(ab) : mx;
+                    }
                 }
             }
         }
@@ -482,12 +485,12 @@ template <int FMT> struct BatchedSolver {
                     for (int i = threadIdx.x; i <= j; i += BT_THREADS) sm->h[i] = sm->tot[i];
                     __syncthreads();
                     double ss, mx;
-                    axpy(a, s, sm, r0, r1, j + 1, sm->h, ss, mx);
+                    axpy<false>(a, s, sm, r0, r1, j + 1, sm->h, ss, mx);   // (norms of w1 unused)
                     dot(a, s, sm, r0, r1, j + 1);
                     team.reduce(sm, j + 1);
                     for (int i = threadIdx.x; i <= j; i += BT_THREADS) sm->u[i] = sm->tot[i];
                     __syncthreads();
-                    axpy(a, s, sm, r0, r1, j + 1, sm->u, ss, mx);
+                    axpy<true>(a, s, sm, r0, r1, j + 1, sm->u, ss, mx);
                     double nv[1] = {ss};
                     block_sum<1>(sm, nv, 1, 0);
                     {   // block max of |w|
