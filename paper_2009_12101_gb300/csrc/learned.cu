@@ -206,6 +206,7 @@ struct BwdSmem {
 };
 
 constexpr int BWD_THREADS = 256;
+static_assert(BWD_THREADS == 2 * BT && NH % 2 == 0, "the row phase of the backward pairs two threads per row");
 constexpr int GPT = (NPARAM + BWD_THREADS - 1) / BWD_THREADS;   // gradient entries per thread (21)
 
 __global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const float* __restrict__ feat,
@@ -222,22 +223,32 @@ __global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long i0 = t * BT;
         __syncthreads();
-        if (threadIdx.x < BT) {
-            const int rr = threadIdx.x;
+        // two threads per row, each taking half of the hidden units of every layer (the
+        // same operations in the same order as one thread per row, so the same values)
+        {
+            const int rr = threadIdx.x % BT, hf = threadIdx.x / BT;
+            const int u0 = hf * (NH / 2), u1 = u0 + NH / 2;
             const long long i = i0 + rr;
             const bool valid = i < n;
             float f[NIN], g[NOUT];
 #pragma unroll
-            for (int k = 0; k < NIN; k++) { f[k] = valid ? feat[i * NIN + k] : 0.f; s.F[rr][k] = f[k]; }
+            for (int k = 0; k < NIN; k++) f[k] = valid ? feat[i * NIN + k] : 0.f;
 #pragma unroll
-            for (int k = 0; k < NOUT; k++) { g[k] = valid ? gout[i * NOUT + k] : 0.f; s.Go[rr][k] = g[k]; }
-            for (int o = 0; o < NH; o++) {
+            for (int k = 0; k < NOUT; k++) g[k] = valid ? gout[i * NOUT + k] : 0.f;
+            if (hf == 0) {
+#pragma unroll
+                for (int k = 0; k < NIN; k++) s.F[rr][k] = f[k];
+#pragma unroll
+                for (int k = 0; k < NOUT; k++) s.Go[rr][k] = g[k];
+            }
+            for (int o = u0; o < u1; o++) {
                 float z = s.p[OFF_B1 + o];
 #pragma unroll
                 for (int k = 0; k < NIN; k++) z = fmaf(s.p[OFF_W1 + o * NIN + k], f[k], z);
                 s.H1[rr][o] = valid ? fmaxf(z, 0.f) : 0.f;
             }
-            for (int o = 0; o < NH; o++) {
+            __syncthreads();                                     // the row's whole H1
+            for (int o = u0; o < u1; o++) {
                 float z = s.p[OFF_B2 + o];
                 for (int q = 0; q < NH; q++) z = fmaf(s.p[OFF_W2 + o * NH + q], s.H1[rr][q], z);
                 float dz = 0.f;
@@ -246,7 +257,8 @@ __global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const
                 s.H2[rr][o] = valid ? fmaxf(z, 0.f) : 0.f;
                 s.D2[rr][o] = (valid && z > 0.f) ? dz : 0.f;
             }
-            for (int q = 0; q < NH; q++) {
+            __syncthreads();                                     // the row's whole D2
+            for (int q = u0; q < u1; q++) {
                 float dz = 0.f;
                 for (int o = 0; o < NH; o++) dz = fmaf(s.p[OFF_W2 + o * NH + q], s.D2[rr][o], dz);
                 s.D1[rr][q] = s.H1[rr][q] > 0.f ? dz : 0.f;
