@@ -205,9 +205,10 @@ struct BwdSmem {
     float Go[BT][NOUT];
 };
 
-constexpr int BWD_THREADS = 256;
-static_assert(BWD_THREADS == 2 * BT && NH % 2 == 0, "the row phase of the backward pairs two threads per row");
-constexpr int GPT = (NPARAM + BWD_THREADS - 1) / BWD_THREADS;   // gradient entries per thread (21)
+constexpr int BWD_THREADS = 512;
+constexpr int TPR = BWD_THREADS / BT;                            // threads per row in the row phase
+static_assert(BWD_THREADS == TPR * BT && NH % TPR == 0, "the row phase splits the hidden units evenly");
+constexpr int GPT = (NPARAM + BWD_THREADS - 1) / BWD_THREADS;   // gradient entries per thread (11)
 
 __global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const float* __restrict__ feat,
                                                               const float* __restrict__ params,
@@ -223,11 +224,12 @@ __global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long i0 = t * BT;
         __syncthreads();
-        // two threads per row, each taking half of the hidden units of every layer (the
-        // same operations in the same order as one thread per row, so the same values)
+        // TPR threads per row, each taking an equal share of the hidden units of every
+        // layer (the same operations in the same order as one thread per row, so the
+        // same values)
         {
             const int rr = threadIdx.x % BT, hf = threadIdx.x / BT;
-            const int u0 = hf * (NH / 2), u1 = u0 + NH / 2;
+            const int u0 = hf * (NH / TPR), u1 = u0 + NH / TPR;
             const long long i = i0 + rr;
             const bool valid = i < n;
             float f[NIN], g[NOUT];
