@@ -5,7 +5,7 @@
  * High Performance GPUs" (arXiv 2009.12101).  Restarted, right-preconditioned GMRES(m)
  * (Fig. 1) whose Krylov basis V is stored in a compact format while the arithmetic
  * keeps FP64 accuracy (Section 3); the basis is decompressed on every read and
- * compressed on every store (Section 4.2, "memory accessor"); fixed-point formats carry
+ * compressed on every store (the memory accessor of Section 4.2); fixed-point formats carry
  * the per-vector scale sigma_j = (||v_j||_inf / ||v_j||_2) / max_intxx (Section 4.2);
  * convergence ||b - A x||_2 <= tau ||b||_2 is confirmed by an explicit residual each
  * time the recurrence residual says so (Section 5.2).
