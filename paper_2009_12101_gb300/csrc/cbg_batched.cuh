@@ -468,10 +468,11 @@ template <int FMT> struct BatchedSolver {
                 int k = 0;
                 for (int j = 0; j < kcap; j++) {
                     team.sync();                               // column j of all blocks visible
-                    // w = A D^{-1} v_j (Jacobi folded into the values), omega
+                    // w = 2^s A D^{-1} v_j (the normalised operator; Jacobi folded into the
+                    // values), omega = ||w||.  Double-float products unless the planes are
+                    // absent; f64 codes keep FP64 products, which measured faster than
+                    // splitting every gathered code.
                     double om[1];
-                    // (double-float products unless the planes are absent; f64 codes keep FP64
-                    // products, which measured faster than splitting every gathered code)
                     const unsigned char* vj = a.V + s.v_off + (long long)j * s.ld * BS;
                     if (FMT != F64 && a.valpdf)
                         om[0] = spmv_df(a, s, sm, r0, r1, vj, sm->scale[j]);   // planes hold 2^s A_pc
