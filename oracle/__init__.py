@@ -1,9 +1,10 @@
 """Plain CPU FP64 oracle for compressed-basis GMRES (arXiv 2009.12101).
 
-TEST INFRASTRUCTURE ONLY.  The oracle is a slow, sequential restatement of the
-method (Fig. 1, Sections 2-5), written in plain C (``cbg_oracle.c``) and loaded here
-with ctypes.  Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
-baseline may import it.  It shares no code with the CUDA library in
+TEST INFRASTRUCTURE ONLY.  The oracle is a slow, plain restatement of the method
+(Fig. 1, Sections 2-5), written in plain C (``cbg_oracle.c``) and loaded here with
+ctypes.  Its loops over rows and over the fixed blocks of inner products may run on
+several host threads (OpenMP); the results do not depend on the thread count.  Only
+the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU baseline may import it.  It shares no code with the CUDA library in
 ``paper_2009_12101_gb300``; neither imports the other.  Parity pins that tie the
 oracle to the paper and to mathematics live in ``tests/test_oracle_*.py``.
 
@@ -38,16 +39,28 @@ ORTHO_CGS, ORTHO_MGS = 0, 1
 OK, NOT_CONVERGED, ERR_ARG, ERR_NONFINITE = 0, 1, -1, -2
 
 
+CFLAGS = ["-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math"]
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no contraction of a*b+c into fma)."""
+    """Compile the oracle with gcc (plain C11, OpenMP, no contraction of a*b+c into fma;
+    no -march=native, so x86 and aarch64 builds round alike)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(__file__))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc"] + CFLAGS + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(t: int) -> None:
+    """Host threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().or_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 class GmresArgs(C.Structure):
@@ -81,6 +94,10 @@ def lib():
             L.or_decode.argtypes = [C.c_int, i64, vp, d, vp]
             L.or_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
             L.or_spmv.restype = None
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_set_threads.restype = None
+            L.or_get_threads.argtypes = []
+            L.or_get_threads.restype = C.c_int
             L.or_dot.argtypes = [i64, vp, vp]
             L.or_dot.restype = d
             L.or_gram_schmidt_pass.argtypes = [i64, vp, i64, C.c_int, vp, vp]

@@ -2,15 +2,44 @@
  * cbg_oracle.c -- plain CPU FP64 oracle for compressed-basis GMRES.
  *
  * TEST INFRASTRUCTURE ONLY (see cbg_oracle.h for what it follows and the readings it
- * takes).  Sequential loops, no blocking, no fused operations: the build uses
- * -ffp-contract=off so that every product and sum is rounded separately, on x86 and
- * on aarch64 alike.
+ * takes).  No fused operations: the build uses -ffp-contract=off so that every product
+ * and sum is rounded separately, on x86 and on aarch64 alike.
+ *
+ * Parallel loops (OpenMP, when the build enables it) only split work whose result does
+ * not depend on the split: rows of a sparse product, elements of a vector update, and
+ * the fixed blocks of an inner product (reading R19: every inner product adds its terms
+ * in index order within blocks of OR_DOT_BLOCK terms, then the block sums in block
+ * order).  One thread and all threads give bitwise the same results.
  */
 #include "cbg_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* loops shorter than this stay on one thread (the parallel region would cost more) */
+#define OR_PAR_MIN 32768
+
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(t < 1 ? 1 : t);
+#else
+    (void)t;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ===================================================================================
  * Scalar codec, written from the format definitions.
@@ -162,18 +191,21 @@ int or_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, dou
     switch (fmt) {
     case OR_F64: {
         double* c = (double*)codes;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) c[i] = v[i];
         *scale = 1.0;
         return OR_OK;
     }
     case OR_F32: {
         float* c = (float*)codes;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) c[i] = (float)v[i];
         *scale = 1.0;
         return OR_OK;
     }
     case OR_F16: {
         uint16_t* c = (uint16_t*)codes;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) c[i] = or_f64_to_f16(v[i]);
         *scale = 1.0;
         return OR_OK;
@@ -183,6 +215,7 @@ int or_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, dou
         double mx = int_max(fmt);
         double sigma = vmax / mx;           /* sigma_j = (||w||_inf/||w||_2) / max_int */
         double inv = 1.0 / sigma;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) {
             double q = rint(v[i] * inv);
             if (q > mx) q = mx;
@@ -196,6 +229,7 @@ int or_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, dou
     case OR_BF16:
     case OR_E4M3: {
         int e = pow2_scale_exponent(vmax, fmt == OR_BF16 ? 1.0 : 448.0);
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) {
             float f = (float)ldexp(v[i], -e);
             if (fmt == OR_BF16) ((uint16_t*)codes)[i] = or_f32_to_bf16(f);
@@ -212,6 +246,8 @@ int or_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, dou
 int or_decode(int fmt, int64_t n, const void* codes, double scale, double* out)
 {
     if (n < 0 || (n > 0 && (!codes || !out))) return OR_ERR_ARG;
+    if (or_format_bytes(fmt) == 0) return OR_ERR_ARG;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; i++) {
         switch (fmt) {
         case OR_F64: out[i] = ((const double*)codes)[i]; break;
@@ -221,7 +257,7 @@ int or_decode(int fmt, int64_t n, const void* codes, double scale, double* out)
         case OR_I16: out[i] = (double)((const int16_t*)codes)[i] * scale; break;
         case OR_BF16: out[i] = or_bf16_to_f64(((const uint16_t*)codes)[i]) * scale; break;
         case OR_E4M3: out[i] = or_e4m3_to_f64(((const uint8_t*)codes)[i]) * scale; break;
-        default: return OR_ERR_ARG;
+        default: break;
         }
     }
     return OR_OK;
@@ -233,6 +269,7 @@ int or_decode(int fmt, int64_t n, const void* codes, double scale, double* out)
 void or_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
              const double* x, double* y)
 {
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; i++) {
         double s = 0.0;
         for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * x[col[p]];
@@ -240,10 +277,25 @@ void or_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
     }
 }
 
+/* sum of a_i b_i (reading R19): terms in index order within each block of OR_DOT_BLOCK,
+ * then the block sums in block order */
 double or_dot(int64_t n, const double* a, const double* b)
 {
+    if (n <= 0) return 0.0;
+    const int64_t nb = (n + OR_DOT_BLOCK - 1) / OR_DOT_BLOCK;
+    double stack_part[64];
+    double* part = nb <= 64 ? stack_part : (double*)malloc((size_t)nb * sizeof(double));
+    if (!part) return NAN;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t k = 0; k < nb; k++) {
+        const int64_t i1 = (k + 1) * OR_DOT_BLOCK < n ? (k + 1) * OR_DOT_BLOCK : n;
+        double s = 0.0;
+        for (int64_t i = k * OR_DOT_BLOCK; i < i1; i++) s += a[i] * b[i];
+        part[k] = s;
+    }
     double s = 0.0;
-    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    for (int64_t k = 0; k < nb; k++) s += part[k];
+    if (part != stack_part) free(part);
     return s;
 }
 
@@ -251,15 +303,18 @@ static double nrm2(int64_t n, const double* a) { return sqrt(or_dot(n, a, a)); }
 
 static double nrminf(int64_t n, const double* a)
 {
-    double m = 0.0;
+    double m = 0.0;   /* the maximum does not depend on the order */
+#pragma omp parallel for schedule(static) reduction(max : m) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; i++) if (fabs(a[i]) > m) m = fabs(a[i]);
     return m;
 }
 
 static int all_finite(int64_t n, const double* a)
 {
-    for (int64_t i = 0; i < n; i++) if (!isfinite(a[i])) return 0;
-    return 1;
+    int ok = 1;
+#pragma omp parallel for schedule(static) reduction(&& : ok) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; i++) ok = ok && isfinite(a[i]);
+    return ok;
 }
 
 typedef struct {
@@ -320,6 +375,7 @@ static void apply_precond(const problem* P, const double* v, double* z)
 {
     int64_t n = P->n;
     if (P->precond == OR_PC_JACOBI) {
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) z[i] = v[i] / P->dinv_src[i];
     } else if (P->precond == OR_PC_SPAI) {
         or_spmv(n, P->rowptr, P->col, P->pvals, v, z);
@@ -344,6 +400,7 @@ static int compress_column(int fmt, int64_t n, const double* w, double h, void* 
                            double* vt, double* tmp)
 {
     double inv = 1.0 / h;
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; i++) tmp[i] = w[i] * inv;
     double vmax = nrminf(n, tmp);
     double scale;
@@ -365,14 +422,18 @@ void or_gram_schmidt_pass(int64_t n, const double* V, int64_t ncols, int ortho, 
         for (int64_t i = 0; i <= j; i++) {
             const double* vi = V + (size_t)i * (size_t)n;
             c[i] = or_dot(n, vi, w);
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * c[i];
         }
         return;
     }
     for (int64_t i = 0; i <= j; i++) c[i] = or_dot(n, V + (size_t)i * (size_t)n, w);
-    for (int64_t i = 0; i <= j; i++) {
-        const double* vi = V + (size_t)i * (size_t)n;
-        for (int64_t t = 0; t < n; t++) w[t] -= vi[t] * c[i];
+    /* w -= V c: every element subtracts its terms in column order 0..j */
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t t = 0; t < n; t++) {
+        double wt = w[t];
+        for (int64_t i = 0; i <= j; i++) wt -= V[(size_t)i * (size_t)n + (size_t)t] * c[i];
+        w[t] = wt;
     }
 }
 
@@ -464,6 +525,7 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
     for (;;) {
         /* Fig. 1, cycle start: r0 = b - A x0, beta = ||r0|| */
         or_spmv(n, rowptr, col, val, x, r);
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t i = 0; i < n; i++) r[i] = b[i] - r[i];
         double beta = nrm2(n, r);
         if (!isfinite(beta)) { a->status = OR_ERR_NONFINITE; break; }
@@ -567,13 +629,15 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
             for (int64_t c = i + 1; c < k; c++) s -= R[i + c * (m + 1)] * y[c];
             y[i] = s / R[i + i * (m + 1)];
         }
-        /* x = x0 + M^{-1} (V_k y) */
-        for (int64_t t = 0; t < n; t++) tmp[t] = 0.0;
-        for (int64_t c = 0; c < k; c++) {
-            const double* vc = V + (size_t)c * (size_t)n;
-            for (int64_t t = 0; t < n; t++) tmp[t] += vc[t] * y[c];
+        /* x = x0 + M^{-1} (V_k y); every element adds its terms in column order */
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+        for (int64_t t = 0; t < n; t++) {
+            double s = 0.0;
+            for (int64_t c = 0; c < k; c++) s += V[(size_t)c * (size_t)n + (size_t)t] * y[c];
+            tmp[t] = s;
         }
         apply_precond(&P, tmp, z);
+#pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
         for (int64_t t = 0; t < n; t++) x[t] += z[t];
         if (!all_finite(n, x)) { a->status = OR_ERR_NONFINITE; break; }
         /* restart (the explicit residual decides) */

@@ -41,6 +41,9 @@
  *       IEEE cast (Section 4.2 lists float16 without scaling).
  *   R7  iterations = Arnoldi steps (sparse products of Fig. 1's Arnoldi step); maxit caps them.
  *   R8  ||b|| = 0 returns x = 0 (exact solution) with zero iterations.
+ *   R19 the order of the terms of an inner product is not given: index order within
+ *       fixed blocks of OR_DOT_BLOCK terms, then the block sums in block order (the
+ *       result does not depend on how many threads run the blocks).
  */
 #ifndef CBG_ORACLE_H
 #define CBG_ORACLE_H
@@ -87,10 +90,17 @@ void or_vec_e4m3_to_f64(int64_t n, const uint8_t* c, double* out);
 int or_encode(int fmt, int64_t n, const double* v, double vmax, void* codes, double* scale);
 int or_decode(int fmt, int64_t n, const void* codes, double scale, double* out);
 
+/* ---- threads ---------------------------------------------------------------------
+ * Threads of the parallel loops (a build with OpenMP; 1 otherwise).  Results do not
+ * depend on the count. */
+void or_set_threads(int t);
+int  or_get_threads(void);
+
 /* ---- building blocks ------------------------------------------------------------- */
+#define OR_DOT_BLOCK 4096
 void   or_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                const double* x, double* y);              /* y = A x, row sums in CSR order */
-double or_dot(int64_t n, const double* a, const double* b); /* sequential sum           */
+double or_dot(int64_t n, const double* a, const double* b); /* blocked sum (R19)        */
 /* one Gram-Schmidt pass of w against the ncols columns of V (n x ncols, column-major):
  * coefficients c (ncols), w reduced in place; ortho = OR_ORTHO_CGS or OR_ORTHO_MGS */
 void   or_gram_schmidt_pass(int64_t n, const double* V, int64_t ncols, int ortho, double* w,

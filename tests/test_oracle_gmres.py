@@ -474,3 +474,45 @@ def test_mgs_arnoldi_relation_and_orthogonality(oracle_lib):
     for j in range(k):
         hm, hc = rm["H1"][: j + 2, j], rc["H1"][: j + 2, j]
         assert np.linalg.norm(hm - hc) <= 1e-12 * np.linalg.norm(hc), j
+
+
+def test_blocked_inner_product_reading_r19():
+    """Inner products follow reading R19 exactly: index order within blocks of 4096 terms,
+    then the block sums in block order (a pure-Python restatement gives the same bits);
+    integer-valued data sums exactly."""
+    rng = np.random.default_rng(19)
+    n = 3 * 4096 + 1234 + 40000          # several blocks, a ragged last block, > the threading threshold
+    a = rng.standard_normal(n) * np.exp(rng.uniform(-20, 20, n))
+    b = rng.standard_normal(n)
+    ref = 0.0
+    for k0 in range(0, n, 4096):
+        s = 0.0
+        for i in range(k0, min(n, k0 + 4096)):
+            s += float(a[i]) * float(b[i])
+        ref += s
+    assert O.dot(a, b) == ref
+    ai = rng.integers(-2 ** 20, 2 ** 20, n).astype(np.float64)
+    bi = rng.integers(-2 ** 10, 2 ** 10, n).astype(np.float64)
+    assert O.dot(ai, bi) == float(int(np.dot(ai.astype(np.int64), bi.astype(np.int64))))
+    assert O.dot(a[:0], b[:0]) == 0.0
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    """The oracle's parallel loops split only work whose result does not depend on the
+    split (rows, elements, fixed inner-product blocks): 1, 3 and all threads give the same
+    bits for x, the Hessenberg matrix and the iteration count."""
+    import os
+    A = W.convdiff3d(40)                 # n = 64,000: above the threading threshold
+    xs = W.exact_solution(A.n, 2)
+    b = W.rhs_from_solution(A, xs)
+    runs = []
+    try:
+        for t in (1, 3, os.cpu_count() or 2):
+            O.set_threads(t)
+            runs.append(O.gmres(A, b, m=30, fmt=O.F16, tol=1e-10, maxit=70, want_H1=True))
+    finally:
+        O.set_threads(os.cpu_count() or 1)
+    for r in runs[1:]:
+        assert r["iters"] == runs[0]["iters"]
+        assert np.array_equal(r["x"], runs[0]["x"])
+        assert np.array_equal(r["H1"], runs[0]["H1"])
