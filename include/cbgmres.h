@@ -191,7 +191,7 @@ int cbgmres_format_bytes(int fmt);
  * basis format `fmt`.  Copies A to library-owned device memory and allocates the basis
  * V ((m+1) columns of n codes, each column padded to a multiple of 4096 elements), the
  * per-vector scales, the Hessenberg and the work vectors once; every solve reuses them.
- * Errors: CBG_ERR_ARG (n < 1, restart < 1 or > 255, bad format, bad CSR bounds when the
+ * Errors: CBG_ERR_ARG (n < 1, restart < 1 or > 319, bad format, bad CSR bounds when the
  * CSR is on the host), CBG_ERR_OOM, CBG_ERR_CUDA.  *out is NULL on error. */
 int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* opt,
                    cbg_handle** out);
@@ -250,7 +250,7 @@ int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int6
  * No counterpart in the paper (its GMRES has one right-hand side); the building block of
  * block Krylov orthogonalisation.  Reads V once for all k vectors (one split-K product
  * in double-float arithmetic, like cbg_basis_dot with arith = CBG_ARITH_DF32).
- *   V: device codes of format fmt, ncols (<= 256) columns of leading dimension ld
+ *   V: device codes of format fmt, ncols (<= 320) columns of leading dimension ld
  *      elements (ld >= n, ld % 4096 == 0, rows n..ld-1 zero);
  *   scales[ncols]: device decode factors;  W: device, n x k column-major, leading
  *      dimension ldw >= n (only rows < n are read);
@@ -275,6 +275,17 @@ int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64
                              int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                              void* stream, int path);
 
+/* Test of the failure path (no counterpart in the paper).  The next `dots` launches of
+ * the pipelined basis dot (DF32 arithmetic) made by solves on h withhold their first
+ * bulk-copy stage -- no arrival, no copies -- and give up their waits after
+ * wait_cycles clock cycles instead of about a second.  Every wait on that stage runs
+ * out, the kernel records the timeout and returns, and the solve returns
+ * CBG_ERR_TIMEOUT at its next synchronisation; no copy is left in flight and the
+ * context stays usable, so the next solve on h runs normally.  Errors: CBG_ERR_ARG
+ * (dots < 0, wait_cycles < 1), CBG_ERR_UNSUPPORTED (the handle uses FP64 arithmetic,
+ * which has no pipelined dot). */
+int cbgmres_test_stall(cbg_handle* h, int dots, long long wait_cycles);
+
 /* Copy the accumulated per-kernel profile of a handle (options.profile == 1) into
  * *out; reset != 0 clears it afterwards.  Errors: CBG_ERR_ARG. */
 int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset);
@@ -286,13 +297,15 @@ int cbgmres_profile(cbg_handle* h, cbg_profile* out, int reset);
  * another allocator (a framework's caching allocator, a fixed pool) cannot count on a
  * private cudaMalloc succeeding, and callers in latency-critical loops cannot accept the
  * device-wide synchronisation of cudaFree.  This variant keeps its scratch in one
- * file-scope device array of about 612 KiB that every GPU loading the library holds
+ * file-scope device array of about 765 KiB that every GPU loading the library holds
  * until the process exits; it calls no cudaMalloc, cudaFree or allocating routine.
- * Limits: ncols <= 256 (larger: CBG_ERR_ARG); the kernel uses at most 304 thread blocks.
- * The first call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  All calls share the one
- * array, so calls whose work overlaps on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  Synchronises `stream`. */
+ * Limits: ncols <= 320 (larger: CBG_ERR_ARG); the kernel uses at most 304 thread blocks.
+ * Every call looks up the array's address on the current device, copies `scales` from
+ * the host, reads h back to the host and synchronises `stream`: it must not be called
+ * while that stream is being captured into a CUDA graph.  All calls share the one
+ * array, which keeps the last call's contents (the call clears what must start at
+ * zero), so calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
 int cbg_basis_dot_noalloc(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
                           const double* scales, const double* w, double* h, void* stream);
 

@@ -103,6 +103,7 @@ def lib():
             L.cbgmres_basis_column.argtypes = [vp, i32, vp]
             L.cbgmres_spmv.argtypes = [vp, vp, vp]
             L.cbgmres_profile.argtypes = [vp, C.POINTER(Profile), i32]
+            L.cbgmres_test_stall.argtypes = [vp, i32, C.c_int64]
             L.cbgmres_destroy.argtypes = [vp]
             L.cbgmres_destroy.restype = None
             L.cbg_encode.argtypes = [i32, i64, vp, d, vp, C.POINTER(d), vp]
@@ -306,6 +307,11 @@ class Solver:
         _check(lib().cbgmres_profile(self._h, C.byref(p), int(reset)), "cbgmres_profile")
         return {c: {"ms": p.ms[i], "bytes": p.bytes[i], "launches": p.launches[i]}
                 for i, c in enumerate(PROFILE_CLASSES)}
+
+    def test_stall(self, dots: int = 1, wait_cycles: int = 2_000_000):
+        """Failure-path test: the next `dots` pipelined dot launches withhold their first
+        bulk-copy stage and give up their waits after `wait_cycles` clock cycles."""
+        _check(lib().cbgmres_test_stall(self._h, int(dots), int(wait_cycles)), "cbgmres_test_stall")
 
     def spmv(self, x):
         torch = _torch()

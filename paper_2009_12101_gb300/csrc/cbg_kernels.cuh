@@ -14,7 +14,7 @@ namespace cbg {
 
 constexpr int THREADS = 256;
 constexpr int TILE_ROWS = 4096;      // ld (padded rows) is a multiple of this
-constexpr int MAXCOLS = 256;         // largest restart length + 1 supported by the kernels
+constexpr int MAXCOLS = 320;         // largest restart length + 1 supported by the kernels
 constexpr int DOT_MIN_ROWS = 1024;   // the dot kernel's grid gives every block >= this many rows
 constexpr int ARITH_DF32 = 0;
 constexpr int ARITH_FP64 = 1;
@@ -130,6 +130,11 @@ struct DotArgs {
     double* out;              // [ncols]
     const int* active;        // skip when *active == 0 (may be null)
     const float* wdf;         // w split into FP32 pairs, planar: hi[nrows] then lo[nrows] (DF32; may be null)
+    // pipelined dot only: waits give up after wait_limit clock cycles (0: the default of
+    // about a second); withhold != 0 makes the producer skip its first work item (no
+    // arrival, no copies), so that the waits on it run out -- a test of the timeout path
+    long long wait_limit;
+    int withhold;
 };
 
 template <int FMT> struct DotCfg {

@@ -96,7 +96,7 @@ template <int COLB>
 __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes, int stages, uint64_t* full,
                                             uint64_t* empty, long long tb, long long te, int ncols, int cg,
                                             const unsigned char* V, long long ldb, const float* wsrc, long long wld,
-                                            int tile_rows, int* failed)
+                                            int tile_rows, int* failed, long long limit, bool withhold)
 {
     const int lane = threadIdx.x & 31;
     const int ngroups = (ncols + cg - 1) / cg;
@@ -109,15 +109,17 @@ __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes
     for (; it < nitems; it++) {
         const int c0 = g * cg;
         const int nc = ncols - c0 < cg ? ncols - c0 : cg;
-        if (it >= stages && !warp_wait(&empty[rg.s], rg.ph ^ 1u)) { *failed = 1; break; }
+        if (it >= stages && !warp_wait(&empty[rg.s], rg.ph ^ 1u, limit)) { *failed = 1; break; }
         unsigned char* st = ring + (size_t)rg.s * stage_bytes;
-        if (lane == 0) mbar_arrive_expect_tx(&full[rg.s], (unsigned)(nc * COLB) + 2u * wplane);
-        __syncwarp();
-        if (lane < nc)
-            bulk_g2s_hint(st + lane * COLB, V + (long long)(c0 + lane) * ldb + t * COLB, COLB, &full[rg.s], pol);
-        if (lane >= 30) {
-            const float* src = wsrc + (lane == 31 ? wld : 0) + t * tile_rows;
-            bulk_g2s(st + cg * COLB + (lane == 31 ? wplane : 0u), src, wplane, &full[rg.s]);
+        if (!(withhold && it == 0)) {
+            if (lane == 0) mbar_arrive_expect_tx(&full[rg.s], (unsigned)(nc * COLB) + 2u * wplane);
+            __syncwarp();
+            if (lane < nc)
+                bulk_g2s_hint(st + lane * COLB, V + (long long)(c0 + lane) * ldb + t * COLB, COLB, &full[rg.s], pol);
+            if (lane >= 30) {
+                const float* src = wsrc + (lane == 31 ? wld : 0) + t * tile_rows;
+                bulk_g2s(st + cg * COLB + (lane == 31 ? wplane : 0u), src, wplane, &full[rg.s]);
+            }
         }
         __syncwarp();
         rg.next(stages);
@@ -127,7 +129,7 @@ __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes
     const long long nd = it < stages ? it : stages;
     for (long long j = 0; j < nd; j++) {
         if (--rg.s < 0) { rg.s = stages - 1; rg.ph ^= 1u; }
-        if (!warp_wait(&full[rg.s], rg.ph)) { *failed = 1; break; }
+        if (!warp_wait(&full[rg.s], rg.ph, limit)) { *failed = 1; break; }
     }
 }
 
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
     __shared__ int failed;
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
     long long tb, te;
     block_tiles(a.nrows / G::TILE, tb, te);
     const int ngroups = (ncols + CG - 1) / CG;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
     if (warp == DOT_CW) {
         int f = 0;
         tma_produce<G::COLB>(ring, G::STAGE_DOT, stages, full, empty, tb, te, ncols, CG, a.V, a.ldb, a.wdf, a.nrows,
-                             G::TILE, &f);
+                             G::TILE, &f, limit, a.withhold != 0);
         if (f) failed = 1;
     } else if (te > tb) {
         const int rgp = warp % TMA_CW, q0 = (warp / TMA_CW) * CGW;
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
 #pragma unroll
             for (int q = 0; q < CGW / 2; q++) { S2[q] = make_float2(0.f, 0.f); C2[q] = make_float2(0.f, 0.f); }
             for (long long t = tb; t < te; t++) {
-                if (!bad && !warp_wait(&full[rg.s], rg.ph)) {
+                if (!bad && !warp_wait(&full[rg.s], rg.ph, limit)) {
                     bad = true;
                     failed = 1;
                 }

@@ -50,21 +50,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 }
 
 // Wait for the completion of the barrier phase with the given parity; false after
-// WAIT_LIMIT_CYCLES without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+// `limit` clock cycles without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = WAIT_LIMIT_CYCLES)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
 // every lane waits (acquiring the data for itself); the warp then agrees, so a timeout
 // in one lane never leaves the others at a warp-wide operation
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity)
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, long long limit = WAIT_LIMIT_CYCLES)
 {
-    const bool ok = mbar_wait(bar, parity);
+    const bool ok = mbar_wait(bar, parity, limit);
     return __all_sync(0xffffffffu, ok);
 }
 

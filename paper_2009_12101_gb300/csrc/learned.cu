@@ -190,7 +190,8 @@ __global__ void k_spai_loss(long long n, const float* __restrict__ out, const fl
 }
 
 // -------------------------------------------------------------------- MLP backward
-// Tiles of BT rows: phase 1 (one thread per row) recomputes the forward pass and writes
+// Tiles of BT rows: phase 1 (TPR threads per row, each an equal share of the hidden
+// units) recomputes the forward pass and writes
 // H1, H2, D2 = relu'(z2) * (W3^T gout), D1 = relu'(z1) * (W2^T D2) to shared memory;
 // phase 2 (all threads) accumulates the weight gradients as small dense products over
 // the tile (gW2 = D2^T H1, gW1 = D1^T F, gW3 = Gout^T H2, bias = column sums) in

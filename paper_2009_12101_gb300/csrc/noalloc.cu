@@ -8,11 +8,10 @@
 // latency-critical loop cannot afford cudaFree, which synchronises the whole device.
 // cbg_basis_dot_noalloc takes the same arguments and keeps its scratch in one
 // file-scope device array instead.  Every GPU that loads this library holds that array
-// (NOALLOC_SCRATCH_BYTES, about 612 KiB) until the process exits.
+// (NOALLOC_SCRATCH_BYTES, about 765 KiB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "../../include/cbgmres.h"
 #include "cbg_launch.h"
@@ -21,7 +20,7 @@ using namespace cbg;
 
 namespace {
 
-constexpr int NOALLOC_MAX_COLS = MAXCOLS;   // columns of V per call (256)
+constexpr int NOALLOC_MAX_COLS = MAXCOLS;   // columns of V per call (320)
 constexpr int NOALLOC_MAX_GRID = 304;       // thread blocks of the dot kernel per call
 // partial sums [grid][MAXCOLS] | scales [MAXCOLS] | result [MAXCOLS] | counter
 constexpr size_t OFF_PART = 0;
@@ -34,25 +33,15 @@ static_assert(NOALLOC_SCRATCH_BYTES < (1u << 20), "keep the resident scratch mod
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
-// Device address of g_noalloc_scratch, looked up once per device (with that device
-// current) on the first call made on it.  The host-side name g_noalloc_scratch is only a
-// stand-in for the symbol and must never be handed to a kernel.
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-double* g_addr[MAX_DEVICES] = {};
-
+// Device address of g_noalloc_scratch on the current device, looked up on every call
+// (cheap next to the call's synchronisation, and never stale: a device reset reloads the
+// module and moves the array).  The host-side name g_noalloc_scratch is only a stand-in
+// for the symbol and must never be handed to a kernel.
 int scratch_for_current_device(double** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CBG_ERR_CUDA;
-    if (dev < 0 || dev >= MAX_DEVICES) return CBG_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CBG_ERR_CUDA;
-        g_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CBG_ERR_CUDA;
+    *out = static_cast<double*>(p);
     return CBG_OK;
 }
 

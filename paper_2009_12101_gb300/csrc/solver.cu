@@ -14,7 +14,13 @@
 //   backsolve y = R^{-1} g; x += M^{-1} (V y)                        (LS update)
 // The host reads the explicit residual once per cycle and polls a mapped flag every
 // `check_every` steps to stop enqueueing once the device has ended the cycle.
+//
+// NVTX ranges (header-only NVTX 3; inert unless a profiler is attached) mark every
+// restart cycle ("cbgmres cycle") and every launch by kernel class ("cbgmres basis_dot",
+// "... basis_axpy", "... spmv", "... store", "... other"), so a profiler can select the
+// launches of one class or one cycle.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -400,6 +406,8 @@ struct cbg_handle {
     int grid_tma = 0;         // bulk-copy pipelined basis kernels: one block per SM
     int fmt0 = 0;             // the handle's basis format (options.adapt may move up from it)
     bool use_tma = false;
+    int test_stall = 0;            // cbgmres_test_stall: pipelined dots still to be stalled
+    long long test_wait = 0;       //   and their wait limit in clock cycles
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> step_ev;
     // launch accounting and optional per-kernel profiling
@@ -420,7 +428,11 @@ void free_handle(cbg_handle* h)
     if (h->own_ppat) { cudaFree(h->prow); cudaFree(h->pcol); }
     cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->wdf); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
     cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
-    cudaFree(h->state_block); cudaFree(h->d.hist);
+    cudaFree(h->state_block);
+    if (h->d.hist) {   // stream-ordered allocation (see run_solve); the frees above synchronised
+        cudaFreeAsync(h->d.hist, 0);
+        cudaStreamSynchronize(0);
+    }
     if (h->flag_host) cudaFreeHost(h->flag_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -479,12 +491,17 @@ void harvest_profile(cbg_handle* h)
     h->prof_used = 0;
 }
 
+const char* const kClassRange[5] = {"cbgmres basis_dot", "cbgmres basis_axpy", "cbgmres spmv", "cbgmres store",
+                                     "cbgmres other"};
+
 template <class F> void launch(cbg_handle* h, int cls, double bytes, F&& f)
 {
     h->launches++;
     const bool prof = h->opt.profile && h->prof_used < (int)h->prof_cls.size();
     if (prof) cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
+    nvtxRangePushA(kClassRange[cls]);
     f();
+    nvtxRangePop();
     if (prof) {
         cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], h->stream);
         h->prof_cls[h->prof_used] = cls;
@@ -640,8 +657,17 @@ void enqueue_step(cbg_handle* h, int j)
     da.out = h->d.h;
     // DF32: the bulk-copy pipelined dot (one block per SM); FP64 keeps the register kernel
     auto run_dot = [&] {
-        if (h->use_tma) op.dot_tma(h->grid_tma, s, da, &h->d.st->fault);
-        else op.dot(h->opt.arith, h->grid_dot, s, da);
+        if (h->use_tma) {
+            DotArgs dt = da;
+            if (h->test_stall > 0) {          // cbgmres_test_stall: this launch times out
+                dt.withhold = 1;
+                dt.wait_limit = h->test_wait;
+                h->test_stall--;
+            }
+            op.dot_tma(h->grid_tma, s, dt, &h->d.st->fault);
+        } else {
+            op.dot(h->opt.arith, h->grid_dot, s, da);
+        }
     };
     auto run_axpy = [&](const AxpyArgs& xa) { op.axpy(h->opt.arith, EPI_SUB, h->grid_axpy, s, xa); };
     AxpyArgs xa{};
@@ -807,10 +833,16 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
         CBG_CUDA(cudaMemsetAsync(x, 0, h->n * sizeof(double), s));
     } else {
         if (hist_cap > h->hist_alloc) {
-            cudaFree(h->d.hist);
+            // stream-ordered, so growing the history buffer does not synchronise the device
+            if (h->d.hist) CBG_CUDA(cudaFreeAsync(h->d.hist, s));
             h->d.hist = nullptr;
-            int rc = dalloc(&h->d.hist, (size_t)hist_cap);
-            if (rc) return rc;
+            h->hist_alloc = 0;
+            cudaError_t e = cudaMallocAsync((void**)&h->d.hist, (size_t)hist_cap * sizeof(double), s);
+            if (e != cudaSuccess) {
+                h->d.hist = nullptr;
+                last_cuda_error = e;
+                return e == cudaErrorMemoryAllocation ? CBG_ERR_OOM : CBG_ERR_CUDA;
+            }
             h->hist_alloc = hist_cap;
         }
         const double target = tol * bnorm;
@@ -851,18 +883,28 @@ int run_solve(cbg_handle* h, const double* b, double* x, double tol, long long m
             prev_beta = hs.beta;
             iters_before = hs.iters;
             cycles++;
+            nvtxRangePushA("cbgmres cycle");
             enqueue_first_vector(h);
             const int kcap = hs.kcap;
             for (int j = 0; j < kcap; j++) {
                 if (j >= L) {
                     // keep at most L steps in flight; stop enqueueing once the cycle ended
-                    CBG_CUDA(cudaEventSynchronize(h->step_ev[j % L]));
+                    if (cudaEventSynchronize(h->step_ev[j % L]) != cudaSuccess) {
+                        nvtxRangePop();
+                        CBG_CUDA(cudaGetLastError());
+                        return CBG_ERR_CUDA;
+                    }
                     if (*(volatile int*)h->flag_host == 0) break;
                 }
                 enqueue_step(h, j);
-                CBG_CUDA(cudaEventRecord(h->step_ev[j % L], s));
+                if (cudaEventRecord(h->step_ev[j % L], s) != cudaSuccess) {
+                    nvtxRangePop();
+                    CBG_CUDA(cudaGetLastError());
+                    return CBG_ERR_CUDA;
+                }
             }
             enqueue_cycle_end(h, x);
+            nvtxRangePop();
             CBG_CUDA(cudaGetLastError());
         }
         if (!std::isfinite(hs.beta)) status = CBG_ERR_NONFINITE;
@@ -1226,6 +1268,15 @@ int cbgmres_basis_column(cbg_handle* h, int col, double* out)
                            h->V + (long long)col * h->ldb, h->n, sc, out);
     CBG_CUDA(cudaGetLastError());
     CBG_CUDA(cudaStreamSynchronize(h->stream));
+    return CBG_OK;
+}
+
+int cbgmres_test_stall(cbg_handle* h, int dots, long long wait_cycles)
+{
+    if (!h || dots < 0 || wait_cycles < 1) return CBG_ERR_ARG;
+    if (!h->use_tma) return CBG_ERR_UNSUPPORTED;
+    h->test_stall = dots;
+    h->test_wait = wait_cycles;
     return CBG_OK;
 }
 

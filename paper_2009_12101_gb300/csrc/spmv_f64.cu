@@ -1,5 +1,6 @@
-// spmv_f64.cu -- SpMV kernels with an FP64 input vector: explicit residual (Fig. 1
-// the residual of Fig. 1), the second stage of A (P v), and the x update's x += P t.
+// spmv_f64.cu -- SpMV kernels with an FP64 input vector: the explicit residual
+// r = b - A x of Fig. 1, the second stage of the preconditioned operator (A z after
+// z = P v), and the solution update's x += P t.
 #include "cbg_launch_impl.cuh"
 namespace cbg {
 void spmv_f64(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a)

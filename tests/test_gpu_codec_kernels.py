@@ -101,7 +101,8 @@ def _random_basis(fmt, n, ncols, ld, seed):
 
 @pytest.mark.parametrize("arith", ["df32", "fp64"])
 @pytest.mark.parametrize("fmt", FORMATS)
-@pytest.mark.parametrize("n,ncols", [(5000, 1), (12289, 13), (40000, 64), (8191, 101), (600000, 40)])
+@pytest.mark.parametrize("n,ncols", [(5000, 1), (12289, 13), (40000, 64), (8191, 101), (600000, 40),
+                                    (20000, 200), (9000, 256), (12289, 301), (4096, 320)])
 def test_basis_dot_and_axpy_parity(fmt, arith, n, ncols):
     torch, cb = need_gpu()
     ld = (n + cb.TILE_ROWS - 1) // cb.TILE_ROWS * cb.TILE_ROWS

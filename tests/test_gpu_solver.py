@@ -20,6 +20,8 @@ def _problem(name):
         A = W.convdiff3d(20); xs = W.exact_solution(A.n, 2)
     elif name == "random27_small":
         A = W.random27(20000, 0.1); xs = W.exact_solution(A.n, 3)
+    elif name == "poisson128":
+        A = W.poisson2d(128); xs = W.exact_solution(A.n, 1)
     else:
         raise ValueError(name)
     return A, xs, W.rhs_from_solution(A, xs)
@@ -150,38 +152,76 @@ def test_full_solve_parity(prob, fmt):
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
-def test_full_size_headline_workload():
+@pytest.mark.parametrize("m,fmt", [(250, "f32"), (250, "f16"), (300, "f64"), (300, "f32"), (300, "i16"),
+                                   (300, "e4m3")])
+def test_long_restart_parity(m, fmt):
+    """Restart lengths of the paper's restart sweep (Section 5.4 goes to m = 300): Poisson
+    128 x 128 needs 250 and 300 steps in its first cycle, so the basis products run with
+    up to m + 1 = 301 columns.  The first 10 Hessenberg columns, then the full solve:
+    iterations within 2 % of the oracle's, x within 1e-6, true residual judged by the
+    oracle's SpMV."""
+    torch, cb = need_gpu()
+    A, xs, b = _problem("poisson128")
+    k, tol = 10, 1e-10
+    r1 = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True)
+    ro = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=tol, maxit=20000)
+    assert ro["status"] == O.OK and ro["cycles"] >= 2     # the first cycle ran all m steps
+    with cb.Solver.from_csr(A, restart=m, fmt=fmt) as s:
+        Hg = s.arnoldi(to_dev(torch, b), torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+        err = col_relerr(Hg, r1["H1"], k)
+        assert np.all(err <= 1e-10), err
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(to_dev(torch, b), xg, tol=tol, maxit=20000)
+    assert st["status"] == 0, st
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(b - O.spmv(A, x)) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_restart_limit():
+    """Restart lengths up to 319 (320 basis columns) are accepted, longer ones rejected."""
+    torch, cb = need_gpu()
+    A, xs, b = _problem("poisson64")
+    with cb.Solver.from_csr(A, restart=319, fmt="f32"):
+        pass
+    with pytest.raises(cb.CbgError):
+        cb.Solver.from_csr(A, restart=320, fmt="f32")
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f64"])
+def test_full_size_headline_workload(fmt):
     """The headline workload at full size, in the configuration bench.py times:
-    conv-diff 128^3 (n = 2,097,152), f32 basis, GMRES(100), default options.
-    - The first 10 raw Hessenberg columns against the oracle (10 oracle steps at this
-      size take about a second; they do not depend on the restart length).
-    - The solve's true residual, recomputed by the oracle's SpMV.
-    - The explicit and recurrence residuals agree.
-    - The f64 basis needs the same number of steps within 2 %."""
+    conv-diff 128^3 (n = 2,097,152), GMRES(100), default options, the f32 basis and its
+    f64-basis baseline.
+    - The first 10 raw Hessenberg columns against the oracle.
+    - The oracle's full solve (about 540 steps; its loops run on all host cores):
+      iterations within 2 % of the oracle's, x within 1e-6 of the oracle's x.
+    - The solve's true residual, recomputed by the oracle's SpMV, and the explicit
+      residual the solver reports."""
     torch, cb = need_gpu()
     A = W.convdiff3d(128)
     xs = W.exact_solution(A.n, 2)
     b = W.rhs_from_solution(A, xs)
     assert A.n == 2_097_152
     k, tol = 10, 1e-10
-    ro = O.gmres(A, b, m=k, fmt=O.FORMATS["f32"], tol=0.0, maxit=k, want_H1=True)
+    r1 = O.gmres(A, b, m=k, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True)
+    ro = O.gmres(A, b, m=100, fmt=O.FORMATS[fmt], tol=tol, maxit=20000)
+    assert ro["status"] == O.OK
     bd = to_dev(torch, b)
-    iters = {}
-    for fmt in ("f32", "f64"):
-        with cb.Solver.from_csr(A, restart=100, fmt=fmt) as s:
-            if fmt == "f32":
-                Hg = s.arnoldi(bd, torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
-                err = col_relerr(Hg, ro["H1"], k)
-                assert np.all(err <= 1e-10), err
-            xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-            st = s.solve(bd, xg, tol=tol, maxit=20000)
-        assert st["status"] == 0, st
-        x = xg.cpu().numpy()
-        r = b - O.spmv(A, x)
-        assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-9)
-        assert abs(st["true_relres"] - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-12
-        iters[fmt] = st["iters"]
-    assert abs(iters["f32"] - iters["f64"]) <= max(1, 0.02 * iters["f64"]), iters
+    with cb.Solver.from_csr(A, restart=100, fmt=fmt) as s:
+        Hg = s.arnoldi(bd, torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+        err = col_relerr(Hg, r1["H1"], k)
+        assert np.all(err <= 1e-10), err
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(bd, xg, tol=tol, maxit=20000)
+    assert st["status"] == 0, st
+    x = xg.cpu().numpy()
+    r = b - O.spmv(A, x)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+    assert abs(st["true_relres"] - np.linalg.norm(r) / np.linalg.norm(b)) <= 1e-12
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
 @pytest.mark.parametrize("arith", ["df32", "fp64"])
@@ -383,3 +423,40 @@ def test_solve_host_matches_device():
         st_d = s.solve(to_dev(torch, b), xd, tol=1e-10, maxit=5000)
     assert st_h["status"] == 0 and st_h["iters"] == st_d["iters"]
     assert np.array_equal(xh, xd.cpu().numpy())
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_dot_wait_timeout_is_reported_and_recoverable(fmt):
+    """Failure detection without a fault: the solver's pipelined dot is told to withhold
+    its first bulk-copy stage (nothing ever arrives on that stage's barrier) and to give
+    up its waits after 2e6 clock cycles (about a millisecond).  The solve must return
+    CBG_ERR_TIMEOUT instead of hanging, and the next solve on the same handle must be
+    correct (iterations and x against the oracle)."""
+    torch, cb = need_gpu()
+    A, xs, b = _problem("convdiff20")
+    m, tol = 100, 1e-10
+    ro = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=tol, maxit=20000)
+    bd = to_dev(torch, b)
+    with cb.Solver.from_csr(A, restart=m, fmt=fmt) as s:
+        s.test_stall(dots=1, wait_cycles=2_000_000)
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(cb.CbgError) as e:
+            s.solve(bd, xg, tol=tol, maxit=20000)
+        assert e.value.status == -5          # CBG_ERR_TIMEOUT
+        torch.cuda.synchronize()             # the context is still usable
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(bd, xg, tol=tol, maxit=20000)
+    assert st["status"] == 0, st
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(b - O.spmv(A, x)) <= tol * np.linalg.norm(b) * (1 + 1e-9)
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_stall_needs_the_pipelined_dot():
+    torch, cb = need_gpu()
+    A, xs, b = _problem("poisson64")
+    with cb.Solver.from_csr(A, restart=20, fmt="f32", arith="fp64") as s:
+        with pytest.raises(cb.CbgError) as e:
+            s.test_stall(1, 1000)
+    assert e.value.status == -6

@@ -1,5 +1,6 @@
-"""The allocation-free basis dot product (cbg_basis_dot_noalloc) against the allocating
-one (cbg_basis_dot), called through the C ABI.
+"""The allocation-free basis dot product (cbg_basis_dot_noalloc), called through the C
+ABI, against the oracle's inner products of the decoded columns and against the
+allocating entry point (cbg_basis_dot).
 
 The no-alloc variant exists for callers that cannot let a library call cudaMalloc /
 cudaFree: applications whose device memory belongs to another allocator, and loops
@@ -16,38 +17,57 @@ from gpu_common import need_gpu, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _basis(fmt, n, ncols, ld, seed):
+def _basis(fmt, n, ncols, ld, w, seed):
+    """Random normalised columns stored in `fmt`; returns the codes, the scales, the
+    oracle's inner products of the decoded columns with w and the columns' norms."""
     rng = np.random.default_rng(seed)
     f = O.FORMATS[fmt]
     codes = np.zeros((ncols, ld), dtype=O.CODE_DTYPE[f])
     scales = np.zeros(ncols)
+    h_o = np.zeros(ncols)
+    vnorm = np.zeros(ncols)
     for k in range(ncols):
-        w = rng.standard_normal(n)
-        c, s, _ = O.compress_roundtrip(f, w, np.linalg.norm(w))
+        v = rng.standard_normal(n)
+        c, s, dec = O.compress_roundtrip(f, v, np.linalg.norm(v))
         codes[k, :n] = c
         scales[k] = s
-    return codes, scales
+        h_o[k] = O.dot(dec, w)
+        vnorm[k] = np.linalg.norm(dec)
+    return codes, scales, h_o, vnorm
+
+
+def _two_calls(torch, cb, fmt, arith, shapes):
+    for call, (n, ncols) in enumerate(shapes):   # two calls in a row
+        ld = (n + cb.TILE_ROWS - 1) // cb.TILE_ROWS * cb.TILE_ROWS
+        w = np.random.default_rng(5 + call).standard_normal(n)
+        codes, scales, h_o, vnorm = _basis(fmt, n, ncols, ld, w, seed=11 + call)
+        Vt = torch.from_numpy(codes.view(np.uint8).reshape(ncols, -1)).cuda()
+        wd = to_dev(torch, w, ld)
+        h_new = cb.basis_dot_noalloc(fmt, arith, n, Vt, ld, scales, wd)
+        h_ref = cb.basis_dot(fmt, arith, n, Vt, ld, scales, wd)
+        # normwise bound, as for the allocating dot: |error| <= 1e-13 ||v|| ||w||
+        tol = 1e-13 * np.linalg.norm(w) * vnorm
+        assert np.all(np.abs(h_new - h_o) <= tol), (call, np.max(np.abs(h_new - h_o) / tol))
+        assert np.all(np.abs(h_new - h_ref) <= tol), (call, np.max(np.abs(h_new - h_ref) / tol))
 
 
 @pytest.mark.parametrize("fmt,arith", [("f32", "df32"), ("i16", "df32"), ("f64", "fp64")])
-def test_noalloc_dot_matches_allocating_dot_twice(fmt, arith):
+def test_noalloc_dot_matches_oracle_twice(fmt, arith):
     torch, cb = need_gpu()
-    for call, (n, ncols) in enumerate([(70001, 57), (9000, 3)]):   # two calls in a row
-        ld = (n + cb.TILE_ROWS - 1) // cb.TILE_ROWS * cb.TILE_ROWS
-        codes, scales = _basis(fmt, n, ncols, ld, seed=11 + call)
-        w = np.random.default_rng(5 + call).standard_normal(n)
-        Vt = torch.from_numpy(codes.view(np.uint8).reshape(ncols, -1)).cuda()
-        wd = to_dev(torch, w, ld)
-        h_ref = cb.basis_dot(fmt, arith, n, Vt, ld, scales, wd)
-        h_new = cb.basis_dot_noalloc(fmt, arith, n, Vt, ld, scales, wd)
-        dec = np.stack([O.decode(O.FORMATS[fmt], codes[k, :n], scales[k]) for k in range(ncols)])
-        tol = 1e-13 * np.linalg.norm(w) * np.linalg.norm(dec, axis=1)
-        assert np.all(np.abs(h_new - h_ref) <= tol), (call, np.max(np.abs(h_new - h_ref) / tol))
+    _two_calls(torch, cb, fmt, arith, [(70001, 57), (9000, 3)])
+
+
+def test_noalloc_dot_full_scratch_span():
+    """ld >= 304 x 1024 rows and 320 columns: the grid reaches its cap of 304 blocks and
+    every region of the static scratch (all partial-sum rows, the scales, the result,
+    the counter) is written, twice in a row."""
+    torch, cb = need_gpu()
+    _two_calls(torch, cb, "f16", "df32", [(401000, 320), (333333, 320)])
 
 
 def test_noalloc_rejects_too_many_columns():
     torch, cb = need_gpu()
-    n, ncols = 4096, 257
+    n, ncols = 4096, 321
     V = torch.zeros((ncols, 4096 * 4), dtype=torch.uint8, device="cuda")
     w = torch.zeros(4096, dtype=torch.float64, device="cuda")
     with pytest.raises(cb.CbgError) as e:
