@@ -56,7 +56,9 @@ def parse():
     p.add_argument("--restart", type=int, default=100)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-steps", type=int, default=30, help="Arnoldi steps of the oracle sample")
+    p.add_argument("--no-fp64", action="store_true", help="skip the native-FP64-arithmetic comparison solves")
+    p.add_argument("--cpu-steps", type=int, default=100,
+                   help="Arnoldi steps of the 1-thread oracle sample (default: one full cycle of m = 100)")
     p.add_argument("--ortho", choices=["cgs", "mgs"], default="cgs",
                    help="orthogonalisation of the single-system solver (Fig. 1's CGS, or MGS)")
     p.add_argument("--batch-nsys", type=int, default=512,
@@ -70,14 +72,28 @@ def parse():
 
 
 # ------------------------------------------------------------------------ clocks
+def smi_gpu_id(local: int) -> str:
+    """The nvidia-smi id of this process's cuda:<local>: its UUID (nvidia-smi indices
+    count physical GPUs and ignore CUDA_VISIBLE_DEVICES), else the visible-devices entry."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = [e.strip() for e in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if e.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region (read only)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+    def __init__(self, local: int):
+        self.idx = smi_gpu_id(local)
         self.proc = None
         self.lines = []
         self.thread = None
@@ -89,9 +105,11 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
-            return
+            return self
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        time.sleep(0.3)
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
@@ -124,7 +142,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "reasons": sorted(reasons), "gpu": self.idx}
 
 
 # ------------------------------------------------------------------------ helpers
@@ -172,9 +190,10 @@ def build_problem(grid: int):
     return A, xs, b
 
 
-def oracle_sample(A, b, fmt: str, steps: int, restart: int):
+def oracle_sample(A, b, fmt: str, steps: int, restart: int, threads: int):
     """Time the oracle (as it stands) on the first `steps` Arnoldi steps of the solve."""
     import oracle as O
+    O.set_threads(threads)
     t0 = time.perf_counter()
     r = O.gmres(A, b, m=restart, fmt=O.FORMATS[fmt], tol=0.0, maxit=steps)
     return time.perf_counter() - t0, r["iters"]
@@ -187,26 +206,112 @@ def run_reference(args):
         return 0
     A, xs, b = build_problem(args.grid)
     steps = max(2, min(args.cpu_steps, 12))
+    threads = os.cpu_count() or 1
     times = {"f64": [], args.headline: []}
     for it in range(args.warmup + args.steps):
         for fmt in times:
-            t, _ = oracle_sample(A, b, fmt, steps, args.restart)
+            t, _ = oracle_sample(A, b, fmt, steps, args.restart, threads)
             if it >= args.warmup:
                 times[fmt].append(t)
     t64 = sum(times["f64"]); th = sum(times[args.headline])
     v = t64 / th
     sample = (f"first {steps} Arnoldi steps of the {WORKLOAD} solve with the f64 and {args.headline} "
-              f"basis, oracle (plain C, sequential), per step")
+              f"basis, oracle (plain C, {threads} host threads), per step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "x", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "ms_per_step": 1000 * (t64 + th) / args.steps,
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "restart": args.restart,
                        "headline_format": args.headline, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "x", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "x", "cores": threads, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": "x", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------------ CPU baseline helpers
+def host_cpu() -> dict:
+    """Host threads and CPU model of this machine (the GPU machine's host when run there)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count() or 1, "model": model}
+
+
+def oracle_timed(threads: int, fn):
+    """Run fn() with the oracle on `threads` host threads; (seconds, result)."""
+    import oracle as O
+    O.set_threads(threads)
+    t0 = time.perf_counter()
+    r = fn()
+    dt = time.perf_counter() - t0
+    O.set_threads(os.cpu_count() or 1)
+    return dt, r
+
+
+def oracle_step_seconds(A, b, fmt: str, restart: int, threads: int, steps: int | None = None, **kw):
+    """Seconds per Arnoldi step of the oracle (as it stands) over its first `steps` steps
+    (default: one full restart cycle, j = 1..restart)."""
+    import oracle as O
+    steps = steps or restart
+    dt, r = oracle_timed(threads, lambda: O.gmres(A, b, m=restart, fmt=O.FORMATS[fmt], tol=0.0, maxit=steps, **kw))
+    return dt / max(1, r["iters"])
+
+
+def cpu_line(value_tts_all: float, tts_one: float | None, gpu_s: float, sample: str, host: dict,
+             extrapolated: bool, **extra) -> dict:
+    """cpu_baseline object: value = oracle time-to-solution / GPU time-to-solution of the
+    line's headline configuration, on all host threads (1-thread figure beside it)."""
+    d = {"value": round(value_tts_all / gpu_s, 2),
+         "unit": "x (oracle time-to-solution / GPU time-to-solution)",
+         "cores": host["nproc"], "kind": "oracle", "sample": sample, "extrapolated": extrapolated,
+         "host": host, "oracle_s_all_threads": round(value_tts_all, 4), "gpu_s": round(gpu_s, 5)}
+    if tts_one is not None:
+        d["oracle_s_1_thread"] = round(tts_one, 4)
+        d["value_1_thread"] = round(tts_one / gpu_s, 2)
+    d.update(extra)
+    return d
+
+
+def roofline_from_profile(prof: dict, fmt: str, kernel_names: dict, peak: float, peak_kind: str) -> dict:
+    """Roofline of the basis-GEMV kernel class (dot or axpy) with the larger share of a
+    profiled solve: algorithmic bytes per launch / average CUDA-event launch time."""
+    cls = max(("basis_dot", "basis_axpy"), key=lambda c: prof[c]["ms"])
+    nl = max(1, prof[cls]["launches"])
+    avg_ms = prof[cls]["ms"] / nl
+    avg_bytes = prof[cls]["bytes"] / nl
+    ach = avg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": f"{kernel_names[cls]} ({fmt})", "achieved": round(ach, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms}
+
+
+def e2e_host_ratio(solvers: dict, base: str, head: str, b: np.ndarray, n: int, tol: float, maxit: int, reps: int):
+    """Same metric end to end through cbgmres_solve_host (pinned host b and x, the copies
+    inside the timed region): time(base) / time(head)."""
+    import torch
+    bh = torch.from_numpy(b).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    te = {}
+    for f in (base, head):
+        ts = []
+        for _ in range(max(1, reps)):
+            xh[:] = 0.0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            solvers[f].solve_host(bh, xh, tol=tol, maxit=maxit)
+            ts.append(time.perf_counter() - t0)
+        te[f] = sum(ts) / len(ts)
+    return {"value": te[base] / te[head], "unit": "x", "h2d_bytes_per_step": 2 * 2 * 8 * n,
+            "d2h_bytes_per_step": 2 * 8 * n, "seconds": {k: round(v, 4) for k, v in te.items()}}
 
 
 # ------------------------------------------------------------------------ batch workload
@@ -229,12 +334,14 @@ def run_batch(args):
     import tempfile
 
     import torch
+    import oracle as O
     import paper_2009_12101_gb300 as cb
     import workloads as W
     cb.ensure_built()
     mats = W.stencil_batch(nsys=args.batch_nsys)
     xs = [W.exact_solution(A.n, 4, salt=i) for i, A in enumerate(mats)]
-    b = np.concatenate([W.rhs_from_solution(A, x) for A, x in zip(mats, xs)])
+    bs_list = [W.rhs_from_solution(A, x) for A, x in zip(mats, xs)]
+    b = np.concatenate(bs_list)
     fmts = ["f64", "f32", "f16"]
     tol, m = 1e-8, 30
     stream = torch.cuda.current_stream()
@@ -253,8 +360,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         for f in fmts:
             x.zero_(); solvers[f].solve(bd, x, tol=tol)
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start(); time.sleep(0.3)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).start()
     torch.cuda.synchronize()
     times = {f: [] for f in fmts}
     outs = {}
@@ -275,11 +381,11 @@ def run_batch(args):
     o = outs["f32"]
     mb = batch_model_bytes(mats, o["iters"], o["restarts"], m, 4)
     achieved = mb / (t["f32"] * 1e-3) / 1e9
-    # the same 512 systems one by one through the single-system solver (f32, Jacobi)
+    # the same systems one by one through the single-system solver (f32, Jacobi)
     seq_ms = None
     if not args.no_cpu:
         tot = 0.0
-        for A, bb in zip(mats, np.split(b, np.cumsum([A.n for A in mats])[:-1])):
+        for A, bb in zip(mats, bs_list):
             with cb.Solver.from_csr(A, restart=m, fmt="f32", precond="jacobi") as s1:
                 bt = torch.from_numpy(bb).cuda(); xt = torch.zeros(A.n, dtype=torch.float64, device="cuda")
                 s1.solve(bt, xt, tol=tol)   # warm
@@ -292,18 +398,41 @@ def run_batch(args):
     bh = torch.from_numpy(b).pin_memory(); xh = torch.zeros(b.size, dtype=torch.float64).pin_memory()
     te = {}
     for f in ("f64", "f32"):
-        xh.zero_()
-        torch.cuda.synchronize(); t0 = time.perf_counter()
-        bdev = bh.cuda(non_blocking=True); xdev = xh.cuda(non_blocking=True)
-        solvers[f].solve(bdev, xdev, tol=tol)
-        xh.copy_(xdev); torch.cuda.synchronize()
-        te[f] = time.perf_counter() - t0
+        ts = []
+        for _ in range(max(1, args.steps)):
+            xh.zero_()
+            torch.cuda.synchronize(); t0 = time.perf_counter()
+            bdev = bh.cuda(non_blocking=True); xdev = xh.cuda(non_blocking=True)
+            solvers[f].solve(bdev, xdev, tol=tol)
+            xh.copy_(xdev); torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        te[f] = sum(ts) / len(ts)
+    # CPU baseline: the oracle's full solves (f32 basis, Jacobi) of every 32nd system on all
+    # host threads and on one, extrapolated to the batch by rows x GPU iterations
+    cpu = None
+    if not args.no_cpu:
+        hc = host_cpu()
+        pick = list(range(0, len(mats), 32))
+        work = lambda idx: sum(mats[i].n * max(1, int(o["iters"][i])) for i in idx)
+        t_all = t_one = 0.0
+        for i in pick:
+            A, bb = mats[i], bs_list[i]
+            solve = lambda: O.gmres(A, bb, m=m, fmt=O.F32, precond=O.PC_JACOBI, tol=tol, maxit=100000)
+            dt, _ = oracle_timed(hc["nproc"], solve); t_all += dt
+            dt, _ = oracle_timed(1, solve); t_one += dt
+        scale = work(range(len(mats))) / work(pick)
+        cpu = cpu_line(t_all * scale, t_one * scale, t["f32"] / 1000,
+                       f"oracle full solves (f32 basis, Jacobi, restart 30, tol 1e-8) of {len(pick)} of the "
+                       f"{len(mats)} systems (every 32nd), extrapolated to the batch by rows x GPU iterations",
+                       hc, True)
     line = {
         "metric": METRIC, "value": round(t["f64"] / t["f32"], 4), "unit": "x", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD.replace("batch512", f"batch{len(mats)}"), "nsys": len(mats), "total_rows": int(b.size), "restart": m,
+        "config": {"workload": BATCH_WORKLOAD.replace("batch512", f"batch{len(mats)}"), "nsys": len(mats),
+                   "total_rows": int(b.size), "restart": m,
                    "tol": tol, "formats": fmts, "schedule_cluster_split": {f: list(v) for f, v in sched.items()},
+                   "value_is": "time(f64 basis) / time(f32 basis), whole batch in one persistent launch",
                    "l2": "no flush: basis of the batch (0.5-2 GB) exceeds the 129 MB L2"},
         "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},
         "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()},
@@ -317,9 +446,9 @@ def run_batch(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "algorithmic_bytes": mb, "note": "model bytes (SpMV + 4 basis passes per step) / batch time"},
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
         "e2e": {"value": te["f64"] / te["f32"], "unit": "x", "h2d_bytes_per_step": 2 * 2 * 8 * int(b.size),
-                "d2h_bytes_per_step": 2 * 8 * int(b.size)},
+                "d2h_bytes_per_step": 2 * 8 * int(b.size), "seconds": {k: round(v, 4) for k, v in te.items()}},
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -345,57 +474,102 @@ def timed_solve(solver, b, x, tol, maxit, stream):
 
 def run_random27(args):
     """bf16 / e4m3 basis with per-vector power-of-two scale vs f64 basis on the random
-    nonsymmetric n = 2^20 matrices; timed: delta 0.1, m 100; sweep: delta x m, once."""
+    nonsymmetric n = 2^20 matrices; timed: delta 0.1, m 100; sweep: delta x m, once.  Each
+    format's solution is compared with the oracle's solution of the timed configuration."""
     import torch
+    import oracle as O
     import paper_2009_12101_gb300 as cb
     import workloads as W
     cb.ensure_built()
     stream = torch.cuda.current_stream()
     fmts = ["f64", "f32", "bf16", "e4m3"]
     tol = 1e-10
-    results, sweep = {}, []
+    results, sweep, xg = {}, [], {}
+    launches = 0
+    peak, kind = measured_peaks()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).start()
     for delta in (0.01, 0.1, 0.5):
         A = W.random27(1 << 20, delta)
         xs = W.exact_solution(A.n, 3)
-        b = torch.from_numpy(W.rhs_from_solution(A, xs)).cuda()
+        bnp = W.rhs_from_solution(A, xs)
+        b = torch.from_numpy(bnp).cuda()
         x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
         for m in (50, 100, 200):
+            timed_cfg = delta == 0.1 and m == 100
             for f in fmts:
-                with cb.Solver.from_csr(A, restart=m, fmt=f, profile=True) as s:
-                    reps = args.steps if (delta == 0.1 and m == 100) else 1
-                    warm = args.warmup if (delta == 0.1 and m == 100) else 0
-                    for _ in range(warm):
-                        timed_solve(s, b, x, tol, args.maxit, stream)
-                    s.profile(reset=True)
-                    ts = []
-                    for _ in range(reps):
-                        t, st = timed_solve(s, b, x, tol, args.maxit, stream)
-                        ts.append(t)
-                    prof = s.profile()
-                    res = float(np.linalg.norm(W.rhs_from_solution(A, x.cpu().numpy()) - b.cpu().numpy())
-                                / np.linalg.norm(b.cpu().numpy()))
-                    err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
-                    row = {"delta": delta, "m": m, "fmt": f, "ms": sum(ts) / len(ts), "iters": st["iters"],
-                           "status": st["status"], "true_relres": res, "x_err_vs_exact": err,
-                           "dot_gbs": (prof["basis_dot"]["bytes"] / prof["basis_dot"]["ms"] / 1e6
-                                       if prof["basis_dot"]["ms"] else None)}
-                    sweep.append(row)
-                    if delta == 0.1 and m == 100:
-                        results[f] = row
+                s = cb.Solver.from_csr(A, restart=m, fmt=f, profile=True)
+                reps = args.steps if timed_cfg else 1
+                for _ in range(args.warmup if timed_cfg else 0):
+                    timed_solve(s, b, x, tol, args.maxit, stream)
+                s.profile(reset=True)
+                ts = []
+                for _ in range(reps):
+                    t, st = timed_solve(s, b, x, tol, args.maxit, stream)
+                    ts.append(t)
+                    if timed_cfg:
+                        launches += st["kernel_launches"]
+                prof = s.profile()
+                xh = x.cpu().numpy()
+                res = float(np.linalg.norm(bnp - O.spmv(A, xh)) / np.linalg.norm(bnp))
+                err = float(np.linalg.norm(xh - xs) / np.linalg.norm(xs))
+                row = {"delta": delta, "m": m, "fmt": f, "ms": sum(ts) / len(ts), "iters": st["iters"],
+                       "status": st["status"], "true_relres": res, "x_err_vs_exact": err,
+                       "dot_gbs": (prof["basis_dot"]["bytes"] / prof["basis_dot"]["ms"] / 1e6
+                                   if prof["basis_dot"]["ms"] else None)}
+                sweep.append(row)
+                if timed_cfg:
+                    results[f] = row
+                    results[f]["roofline"] = roofline_from_profile(
+                        prof, f, {"basis_dot": "k_basis_dot_tma", "basis_axpy": "k_basis_axpy"}, peak, kind)
+                    xg[f] = xh.copy()
+                    if f in ("f64", "bf16"):
+                        results[f]["solver"] = s
+                        continue
+                s.close()
+        if delta == 0.1:
+            A01, b01 = A, bnp
+    clk = clocks.stop()
     t = {f: results[f]["ms"] for f in fmts}
-    peak, kind = measured_peaks()
+    # each format against the oracle's solution (north_star: the error against the FP64
+    # oracle per format), and the oracle's time-to-solution as the CPU baseline
+    hc = host_cpu()
+    per_fmt = {}
+    t_oracle = {}
+    for f in fmts:
+        dt, ro = oracle_timed(hc["nproc"], lambda: O.gmres(A01, b01, m=100, fmt=O.FORMATS[f], tol=tol,
+                                                            maxit=args.maxit))
+        t_oracle[f] = dt
+        per_fmt[f] = {"oracle_iters": int(ro["iters"]), "gpu_iters": int(results[f]["iters"]),
+                      "x_relerr_vs_oracle": float(np.linalg.norm(xg[f] - ro["x"]) / np.linalg.norm(ro["x"])),
+                      "x_relerr_vs_f64_oracle": None, "oracle_true_relres": float(ro["true_relres"])}
+        if f == "f64":
+            x64o = ro["x"]
+    for f in fmts:
+        per_fmt[f]["x_relerr_vs_f64_oracle"] = float(np.linalg.norm(xg[f] - x64o) / np.linalg.norm(x64o))
+    cpu = None
+    if not args.no_cpu:
+        s1 = oracle_step_seconds(A01, b01, "bf16", 100, 1, steps=20)
+        cpu = cpu_line(t_oracle["bf16"], s1 * results["bf16"]["iters"], t["bf16"] / 1000,
+                       f"oracle full solve of the timed configuration (delta 0.1, m 100, bf16 basis) on all host "
+                       f"threads; 1 thread: the first 20 steps, extrapolated by the solve's steps", hc, False,
+                       oracle_s_all_threads_by_format={f: round(v, 4) for f, v in t_oracle.items()})
+    e2e = e2e_host_ratio({f: results[f]["solver"] for f in ("f64", "bf16")}, "f64", "bf16", b01, A01.n, tol,
+                         args.maxit, args.steps)
+    for f in ("f64", "bf16"):
+        results[f].pop("solver").close()
     line = {"metric": METRIC, "value": round(t["f64"] / t["bf16"], 4), "unit": "x", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
             "config": {"workload": R27_WORKLOAD, "timed": "delta 0.1, m 100", "headline_format": "bf16",
+                       "value_is": "time(f64 basis) / time(bf16 basis)",
                        "formats": fmts, "l2": "no flush: basis >= 0.2 GB exceeds L2"},
             "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},
             "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()},
-            "roofline": {"bound": "hbm", "kernel": "k_basis_dot (bf16, df32)",
-                         "achieved": round(results["bf16"]["dot_gbs"] or 0, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round((results["bf16"]["dot_gbs"] or 0) / peak, 4), "traffic": None,
-                         "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)"},
-            "sweep": sweep, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+            "error_vs_oracle": per_fmt,
+            "roofline": results["bf16"]["roofline"],
+            "roofline_by_format": {f: results[f]["roofline"] for f in fmts},
+            "sweep": [{k: v for k, v in r.items() if k != "roofline"} for r in sweep],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -407,6 +581,7 @@ L96_WORKLOAD = "diffusion3d_cc96_lognormal1_learnedSPAI_f32_restart100_tol1e-10"
 def run_learned96(args):
     """Per-row MLP SPAI trained on 2000 (r, e) pairs from FP64 GMRES, vs Jacobi and none."""
     import torch
+    import oracle as O
     import paper_2009_12101_gb300 as cb
     import workloads as W
     cb.ensure_built()
@@ -414,9 +589,11 @@ def run_learned96(args):
     N = 96
     A = W.diffusion3d_cc(N)[0]
     xs = W.exact_solution(A.n, 5)
-    b = torch.from_numpy(W.rhs_from_solution(A, xs)).cuda()
+    bnp = W.rhs_from_solution(A, xs)
+    b = torch.from_numpy(bnp).cuda()
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     gen = torch.Generator(device="cuda"); gen.manual_seed(20201206)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).start()
     spai = cb.LearnedSpai(A, N, N * N)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -428,30 +605,56 @@ def run_learned96(args):
     l0, l1 = spai.train(steps=400, lr=3e-3)
     e1.record(stream); torch.cuda.synchronize()
     t_train = e0.elapsed_time(e1)
+    train_info = spai.train_stats() if hasattr(spai, "train_stats") else {}
     pv = spai.values()
-    out = {}
+    out, solvers, launches = {}, {}, 0
+    peak, kind = measured_peaks()
+    roof = None
     for pc in ("none", "jacobi", "spai"):
-        with cb.Solver.from_csr(A, restart=100, fmt="f32", precond=pc) as s:
-            if pc == "spai":
-                s.set_spai(pv)
-            for _ in range(args.warmup):
-                timed_solve(s, b, x, 1e-10, args.maxit, stream)
-            ts = []
-            for _ in range(args.steps):
-                t, st = timed_solve(s, b, x, 1e-10, args.maxit, stream)
-                ts.append(t)
-            res = float(np.linalg.norm(W.rhs_from_solution(A, x.cpu().numpy()) - b.cpu().numpy())
-                        / np.linalg.norm(b.cpu().numpy()))
-            out[pc] = {"ms": sum(ts) / len(ts), "iters": st["iters"], "status": st["status"], "true_relres": res}
+        s = cb.Solver.from_csr(A, restart=100, fmt="f32", precond=pc, profile=True)
+        if pc == "spai":
+            s.set_spai(pv)
+        for _ in range(args.warmup):
+            timed_solve(s, b, x, 1e-10, args.maxit, stream)
+        s.profile(reset=True)
+        ts = []
+        for _ in range(args.steps):
+            t, st = timed_solve(s, b, x, 1e-10, args.maxit, stream)
+            ts.append(t)
+            launches += st["kernel_launches"]
+        if pc == "spai":
+            roof = roofline_from_profile(s.profile(), "f32, learned SPAI",
+                                         {"basis_dot": "k_basis_dot_tma", "basis_axpy": "k_basis_axpy"}, peak, kind)
+        res = float(np.linalg.norm(bnp - O.spmv(A, x.cpu().numpy())) / np.linalg.norm(bnp))
+        out[pc] = {"ms": sum(ts) / len(ts), "iters": st["iters"], "status": st["status"], "true_relres": res}
+        solvers[pc] = s
+    clk = clocks.stop()
+    cpu = None
+    if not args.no_cpu:
+        hc = host_cpu()
+        pvh = pv.cpu().numpy()
+        kw = dict(precond=O.PC_SPAI, pvals=pvh)
+        s_all = oracle_step_seconds(A, bnp, "f32", 100, hc["nproc"], **kw)
+        s_one = oracle_step_seconds(A, bnp, "f32", 100, 1, steps=25, **kw)
+        it = out["spai"]["iters"]
+        cpu = cpu_line(s_all * it, s_one * it, out["spai"]["ms"] / 1000,
+                       f"oracle with the trained SPAI (f32 basis): one full restart cycle (100 steps) on all "
+                       f"host threads, the first 25 steps on 1 thread; time-to-solution extrapolated by the "
+                       f"solve's {it} steps", hc, True)
+    e2e = e2e_host_ratio(solvers, "jacobi", "spai", bnp, A.n, 1e-10, args.maxit, args.steps)
+    for s in solvers.values():
+        s.close()
     line = {"metric": METRIC, "value": round(out["jacobi"]["ms"] / out["spai"]["ms"], 4), "unit": "x",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sum(v["ms"] for v in out.values()), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
             "config": {"workload": L96_WORKLOAD, "value_is": "time(Jacobi) / time(learned SPAI), f32 basis",
-                       "pairs": spai.npairs, "train_steps": 400},
-            "solves": out, "train": {"pairs_ms": t_pairs, "train_ms": t_train, "loss_first": l0, "loss_last": l1},
+                       "pairs": spai.npairs, "train_steps": 400,
+                       "l2": "no flush: basis (0.36 GB) exceeds the 129 MB L2"},
+            "solves": out,
+            "train": {"pairs_ms": t_pairs, "train_ms": t_train, "loss_first": l0, "loss_last": l1, **train_info},
             "speedup_learned_vs_none": round(out["none"]["ms"] / out["spai"]["ms"], 4),
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     spai.close()
     print(json.dumps(line), flush=True)
     return 0
@@ -459,7 +662,7 @@ def run_learned96(args):
 
 # ------------------------------------------------------------------------ restart sweep (E6)
 def run_restart_sweep(args):
-    """10 fixed restart cycles for m = 10..250, every format, numerics ignored: the speedup
+    """10 fixed restart cycles for m = 10..300, every format, numerics ignored: the speedup
     over the f64 basis as the basis share of the traffic grows (Section 5.4, Fig. restart)."""
     import torch
     import paper_2009_12101_gb300 as cb
@@ -469,17 +672,50 @@ def run_restart_sweep(args):
     b = torch.from_numpy(bnp).cuda()
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     fmts = ["f64", "f32", "f16", "bf16", "e4m3", "i32", "i16"]
-    rows = []
-    for m in (10, 25, 50, 100, 150, 200, 250):
+    peak, kind = measured_peaks()
+    rows, launches, roof = [], 0, None
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).start()
+    keep = {}
+    for m in (10, 25, 50, 100, 150, 200, 250, 300):
         t = {}
         for f in fmts:
-            with cb.Solver.from_csr(A, restart=m, fmt=f) as s:
-                timed_solve(s, b, x, 0.0, 10 * m, stream)
-                tt, st = timed_solve(s, b, x, 0.0, 10 * m, stream)
-                t[f] = tt
+            s = cb.Solver.from_csr(A, restart=m, fmt=f, profile=True)
+            timed_solve(s, b, x, 0.0, 10 * m, stream)
+            s.profile(reset=True)
+            tt, st = timed_solve(s, b, x, 0.0, 10 * m, stream)
+            launches += st["kernel_launches"]
+            t[f] = tt
+            if m == 300 and f == "f32":
+                roof = roofline_from_profile(s.profile(), "f32, m 300",
+                                             {"basis_dot": "k_basis_dot_tma", "basis_axpy": "k_basis_axpy"}, peak, kind)
+            if m == 100 and f in ("f64", "f32"):
+                keep[f] = s
+            else:
+                s.close()
         rows.append({"m": m, "ms": t, "speedup_vs_f64": {f: round(t["f64"] / v, 4) for f, v in t.items()}})
-    print(json.dumps({"metric": METRIC, "workload": f"restart_sweep_{WORKLOAD}", "cycles": 10, "rows": rows}),
-          flush=True)
+    clk = clocks.stop()
+    cpu = None
+    t100 = rows[3]["ms"]["f32"] / 1000
+    if not args.no_cpu:
+        hc = host_cpu()
+        s_all = oracle_step_seconds(A, bnp, "f32", 100, hc["nproc"])
+        s_one = oracle_step_seconds(A, bnp, "f32", 100, 1, steps=25)
+        cpu = cpu_line(s_all * 1000, s_one * 1000, t100,
+                       "oracle, m = 100, f32 basis: one full restart cycle on all host threads, the first 25 "
+                       "steps on 1 thread; the 10 fixed cycles (1000 steps) extrapolated", hc, True)
+    e2e = e2e_host_ratio(keep, "f64", "f32", bnp, A.n, 0.0, 1000, 1)
+    for s in keep.values():
+        s.close()
+    line = {"metric": METRIC, "value": rows[-1]["speedup_vs_f64"]["f32"], "unit": "x", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": round(sum(sum(r["ms"].values()) for r in rows), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+            "config": {"workload": f"restart_sweep_{WORKLOAD}", "cycles": 10,
+                       "value_is": "time(f64 basis) / time(f32 basis) at m = 300; rows: every m and format",
+                       "l2": "no flush: every basis exceeds the 129 MB L2"},
+            "rows": rows, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": dict(e2e, note="m = 100, 10 fixed cycles, f64 / f32 basis"),
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -489,6 +725,7 @@ def run_multirhs(args):
     on the tensor cores (tcgen05, exact digit products) and on the CUDA cores (double-float),
     the f32 basis on the CUDA cores, and 8 single-vector launches for comparison."""
     import torch
+    import oracle as O
     import paper_2009_12101_gb300 as cb
     cb.ensure_built()
     n, ncols, k = 1 << 21, 100, 8
@@ -497,9 +734,11 @@ def run_multirhs(args):
     stream = torch.cuda.current_stream()
     v32 = rng.standard_normal((ncols, ld)) / np.sqrt(n)
     V32 = torch.from_numpy(v32.astype(np.float32)).cuda().view(torch.uint8)
-    V16 = torch.from_numpy(v32.astype(np.float16)).cuda().view(torch.uint8)
+    v16 = v32.astype(np.float16)
+    V16 = torch.from_numpy(v16).cuda().view(torch.uint8)
     scales = torch.ones(ncols, dtype=torch.float64, device="cuda")      # resident, like V and W
-    W = torch.from_numpy(rng.standard_normal((k, n))).cuda()
+    Wnp = rng.standard_normal((k, n))
+    W = torch.from_numpy(Wnp).cuda()
     ws = torch.empty(cb.lib().cbg_basis_dot_multi_workspace(ld, ncols, k), dtype=torch.uint8, device="cuda")
     H = torch.empty(ncols, k, dtype=torch.float64, device="cuda")
     H1 = [torch.empty(ncols, 1, dtype=torch.float64, device="cuda") for _ in range(k)]
@@ -511,6 +750,7 @@ def run_multirhs(args):
                                                         path="tensor", out=H1[r]) for r in range(k)],
     }
     out = {}
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).start()
     for name, fn in cases.items():
         for _ in range(args.warmup):
             fn()
@@ -522,9 +762,38 @@ def run_multirhs(args):
         e1.record(stream)
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    launches = args.steps * (2 + 2 + 2 + 2 * k)     # product + reduction kernels per call
     Ht = cases["f16_tensor_k8"]().cpu().numpy().copy()
     Hc = cases["f16_cuda_k8"]().cpu().numpy().copy()
     agree = float(np.max(np.abs(Ht - Hc)) / np.max(np.abs(Hc)))
+    # end to end: W from pinned host memory, the product, H back to the host
+    Wh = torch.from_numpy(Wnp).pin_memory()
+    Hh = torch.empty(ncols, k, dtype=torch.float64).pin_memory()
+    te = {}
+    for path in ("cuda", "tensor"):
+        ts = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize(); t0 = time.perf_counter()
+            Wd = Wh.cuda(non_blocking=True)
+            cb.basis_dot_multi("f16", n, V16, ld, scales, Wd, workspace=ws, path=path, out=H)
+            Hh.copy_(H); torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        te[path] = sum(ts) / len(ts)
+    e2e = {"value": te["cuda"] / te["tensor"], "unit": "x", "h2d_bytes_per_step": 8 * k * n,
+           "d2h_bytes_per_step": 8 * k * ncols, "seconds": {p: round(v, 5) for p, v in te.items()}}
+    cpu = None
+    if not args.no_cpu:
+        hc = host_cpu()
+        cols = list(range(0, ncols, 10))            # 10 of the 100 columns, all 8 vectors
+        dec = [O.decode(O.F16, v16[c].view(np.uint16), 1.0) for c in cols]
+        fn = lambda: [[O.dot(d, Wnp[r]) for r in range(k)] for d in dec]
+        t_all, _ = oracle_timed(hc["nproc"], fn)
+        t_one, _ = oracle_timed(1, fn)
+        sc = ncols / len(cols)
+        cpu = cpu_line(t_all * sc, t_one * sc, out["f16_tensor_k8"] / 1000,
+                       "oracle inner products of 10 of the 100 decoded f16 columns with all 8 vectors, "
+                       "extrapolated to the 100 x 8 product", hc, True)
     peak, kind = measured_peaks()
     vbytes16 = ncols * n * 2 + k * n * 8                     # algorithmic bytes: V codes + W
     tflops = 2 * 2 * 128 * 112 * n / (out["f16_tensor_k8"] * 1e-3) / 1e12   # 2 V slices, M = 128, N = 112
@@ -533,7 +802,8 @@ def run_multirhs(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 digits / fp32 accumulate",
             "data": "synthetic",
             "config": {"workload": "multirhs_n2097152_cols100_k8",
-                       "value_is": "time(f16 basis, CUDA cores) / time(f16 basis, tensor cores)"},
+                       "value_is": "time(f16 basis, CUDA cores) / time(f16 basis, tensor cores)",
+                       "l2": "no flush: V (0.42 GB f16) exceeds the 129 MB L2"},
             "ms": {kk: round(v, 4) for kk, v in out.items()},
             "tensor_vs_cuda_max_rel_diff": agree,
             "roofline": {"bound": "hbm", "kernel": "k_dot_multi_tc (f16 basis, k = 8)",
@@ -541,7 +811,7 @@ def run_multirhs(args):
                          "unit": "GB/s", "frac": round(vbytes16 / (out["f16_tensor_k8"] * 1e-3) / 1e9 / peak, 4),
                          "traffic": None, "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)",
                          "tensor_tflops_issued": round(tflops, 1)},
-            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -607,9 +877,7 @@ def main():
     for s in solvers.values():
         s.profile(reset=True)
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+    clocks = ClockSampler(local).start()
     barrier()
     g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
     g0.record(stream)
@@ -676,17 +944,54 @@ def main():
                "h2d_bytes_per_step": 2 * 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n,
                "seconds": {k: round(v, 4) for k, v in te.items()}}
 
-    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    # FP64 arithmetic beside the double-float reading: the same solves with native FP64
+    # basis products and SpMV (what the paper's arithmetic costs on this GPU)
+    arith64 = None
+    if args.arith == "df32" and not args.no_fp64:
+        reps = max(1, min(args.steps, 3))
+        s64 = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith="fp64", precond=args.precond,
+                                     ortho=args.ortho) for f in ("f64", args.headline)}
+        clocks64 = ClockSampler(local).start()
+        t64a, it64a = {}, {}
+        for f, s in s64.items():
+            timed_solve(s, bd, x, args.tol, args.maxit, stream)
+            ts = []
+            for _ in range(reps):
+                tt, st = timed_solve(s, bd, x, args.tol, args.maxit, stream)
+                ts.append(tt)
+            t64a[f], it64a[f] = sum(ts) / len(ts), st["iters"]
+            s.close()
+        clk64 = clocks64.stop()
+        if world > 1:
+            t64a = max_over_ranks(t64a, "cuda")
+        arith64 = {"time_to_solution_s": {f: round(v / 1000, 4) for f, v in t64a.items()},
+                   "speedup_vs_f64": {f: round(t64a["f64"] / v, 4) for f, v in t64a.items()},
+                   "iterations": it64a,
+                   "double_float_gain": {f: round(t64a[f] / t_fmt[f], 4) for f in t64a},
+                   "note": "basis products and per-step SpMV in native FP64 (CBG_ARITH_FP64), same solves; "
+                           "double_float_gain = time(FP64 arithmetic) / time(double-float arithmetic)",
+                   "solves_per_format": reps, "clocks": clk64}
+
+    # CPU baseline: the oracle (rank 0, N = 1 only) over one full restart cycle per
+    # format on all host threads, and on one thread for the headline format; the
+    # time-to-solution is extrapolated with the solve's step count
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        t64, it = oracle_sample(A, b, "f64", args.cpu_steps, args.restart)
-        th, _ = oracle_sample(A, b, args.headline, args.cpu_steps, args.restart)
-        gpu_step_ms = {f: t_fmt[f] / max(1, stats[f]["iters"]) for f in ("f64", args.headline)}
-        cpu = {"value": t64 / th, "unit": "x", "cores": 1, "kind": "oracle",
-               "sample": (f"first {args.cpu_steps} Arnoldi steps (j = 1..{args.cpu_steps}) of the "
-                          f"{WORKLOAD} solve, f64 and {args.headline} basis, sequential C oracle"),
-               "oracle_ms_per_step": {"f64": 1000 * t64 / it, args.headline: 1000 * th / it},
-               "gpu_ms_per_step_full_solve": gpu_step_ms}
+        hc = host_cpu()
+        hf = args.headline
+        s_all = {f: oracle_step_seconds(A, b, f, args.restart, hc["nproc"]) for f in ("f64", hf)}
+        s_one = oracle_step_seconds(A, b, hf, args.restart, 1, steps=args.cpu_steps)
+        tts_all = {f: s_all[f] * stats[f]["iters"] for f in s_all}
+        cpu = cpu_line(tts_all[hf], s_one * stats[hf]["iters"], t_fmt[hf] / 1000,
+                       (f"oracle (plain C, {hc['nproc']} host threads): one full restart cycle (Arnoldi steps "
+                        f"j = 1..{args.restart}) of the {WORKLOAD} solve with the {hf} and f64 basis; 1 thread: "
+                        f"the first {args.cpu_steps} steps with the {hf} basis; time-to-solution extrapolated "
+                        f"as seconds per step x the solve's steps ({stats[hf]['iters']})"),
+                       hc, True,
+                       oracle_s_per_step_all_threads={f: round(v, 5) for f, v in s_all.items()},
+                       oracle_s_per_step_1_thread={hf: round(s_one, 5)},
+                       oracle_time_to_solution_s_all_threads={f: round(v, 3) for f, v in tts_all.items()},
+                       oracle_f64_over_headline=round(tts_all["f64"] / tts_all[hf], 4))
 
     if rank == 0:
         line = {
@@ -713,6 +1018,7 @@ def main():
             "true_relres": {f: stats[f]["true_relres"] for f in fmts},
             "status": {f: stats[f]["status"] for f in fmts},
             "roofline": roofline,
+            "arith_fp64": arith64,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -406,7 +406,7 @@ def test_create_rejects_bad_input():
     with pytest.raises(cb.CbgError):
         cb.Solver(A.rowptr, A.col, A.val, restart=0)
     with pytest.raises(cb.CbgError):
-        cb.Solver(A.rowptr, A.col, A.val, restart=300)
+        cb.Solver(A.rowptr, A.col, A.val, restart=320)
     a = np.array([[0.0, 1.0], [1.0, 0.0]])
     Z = W.from_dense(a)
     with pytest.raises(cb.CbgError):
