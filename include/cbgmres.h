@@ -356,8 +356,12 @@ int cbgmres_solve_fallback(cbg_handle* const* hs, int nh, const double* b, doubl
 /* ---- learned sparse approximate inverse (no counterpart in the paper) ---------------
  * A per-row MLP (inputs: the row's 7-point stencil coefficients divided by a_ii, in the
  * order -z,-y,-x,centre,+x,+y,+z with 0 for a missing neighbour; layers 7 -> 64 -> 64 -> 7
- * with ReLU; BF16 weights, FP32 accumulation) emits P on A's pattern,
- * P_{i,nb(i,k)} = out_k(i) / a_ii, for use as the right preconditioner (CBG_PC_SPAI).
+ * with ReLU) emits P on A's pattern, P_{i,nb(i,k)} = out_k(i) / a_ii, for use as the right
+ * preconditioner (CBG_PC_SPAI).  The network runs on the tensor cores (tcgen05): weights,
+ * features, activations and output gradients enter as BF16, every product sum
+ * accumulates in FP32; biases, ReLU and the loss are FP32; gradients are summed over
+ * CTAs in FP64.  One training step is one fused pass over the rows (forward, loss,
+ * backward, weight gradients) and an Adam update of FP32 master weights.
  * Training minimises mean over pairs of ||P r - e||^2 / ||e||^2 on pairs (r = A e,
  * e = x* - x_k); each pair is folded into per-row statistics on arrival.
  * create: A must be a 3D 7-point pattern with line stride sx and plane stride sxy (host
@@ -375,9 +379,12 @@ int cbg_spai_values(cbg_spai* s, double* pvals);
 int cbg_spai_params(cbg_spai* s, float* params, int set);
 int cbg_spai_num_params(void);
 void cbg_spai_destroy(cbg_spai* s);
-/* One forward / backward of the MLP with given FP32 parameters (host; rounded to BF16):
- * feat (device, rows x 7 FP32) -> out (device, rows x 7); gout (device, rows x 7) ->
- * grad (host, cbg_spai_num_params() FP64, summed over rows).  For gradient checks. */
+/* One forward / backward of the MLP with given FP32 parameters (host; rounded to BF16),
+ * on the same tensor-core kernel as training: feat (device, rows x 7 FP32, 16-byte
+ * aligned) -> out (device, rows x 7); gout (device, rows x 7, 16-byte aligned) -> grad
+ * (host, cbg_spai_num_params() FP64, summed over rows).  For gradient checks.  Errors:
+ * CBG_ERR_ARG (sizes, null or misaligned pointers), CBG_ERR_TIMEOUT (a tensor-core wait
+ * ran out), CBG_ERR_CUDA. */
 int cbg_mlp_forward(int64_t rows, const float* feat, const float* params, float* out, void* stream);
 int cbg_mlp_backward(int64_t rows, const float* feat, const float* params, const float* gout,
                      double* grad, void* stream);

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcbgmres.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["solver.cu", "spmv_f64.cu", "noalloc.cu", "batched.cu", "learned.cu", "multi.cu", "multi_tc.cu"] + [f"basis_{f}.cu" for f in
+SOURCES = ["solver.cu", "spmv_f64.cu", "noalloc.cu", "batched.cu", "learned.cu", "mlp_tc.cu", "multi.cu",
+           "multi_tc.cu"] + [f"basis_{f}.cu" for f in
                                           ("f64", "f32", "f16", "bf16", "e4m3", "i32", "i16")]
 
 

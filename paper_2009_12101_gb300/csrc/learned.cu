@@ -7,8 +7,9 @@
 // L is quadratic in each row's seven P values, so the pairs enter only through per-row
 // statistics G_i = sum w r_nb r_nb^T (7x7), c_i = sum w e_i r_nb, d_i = sum w e_i^2
 // (w = 1/||e||^2), accumulated on the GPU as pairs arrive; every training step is then
-// one MLP forward and backward over the rows.  Weights are BF16 values (FP32 master copy
-// updated by Adam), all sums accumulate in FP32, the cross-block gradient sum in FP64.
+// one fused pass of the network over the rows on the tensor cores (mlp_tc.cu: forward,
+// loss, backward, weight gradients), the cross-CTA gradient sum in FP64 and an Adam
+// update of the FP32 master weights, which the network uses rounded to BF16.
 // The paper has no learned preconditioner; it composes with any preconditioner.
 #include <cuda_runtime.h>
 
@@ -21,6 +22,7 @@
 
 #include "../../include/cbgmres.h"
 #include "cbg_device.cuh"
+#include "cbg_mlp.h"
 
 using namespace cbg;
 
@@ -28,11 +30,7 @@ void cbg_record_cuda_error(cudaError_t e);   // solver.cu
 
 namespace {
 
-constexpr int NIN = 7, NH = 64, NOUT = 7;
-constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NIN, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
-              OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NOUT * NH, NPARAM = OFF_B3 + NOUT;   // 5127
 constexpr int LT = 256;            // threads of the row kernels
-constexpr int BT = 128;            // rows per tile of the backward kernel
 
 __global__ void k_spai_setup(const int* rowptr, const int* col, const double* val, long long n, long long sx,
                              long long sxy, signed char* slot, float* feat, double* diag, unsigned char* mask,
@@ -113,196 +111,6 @@ __global__ void k_pair_accumulate(const int* rowptr, const int* col, const signe
     }
 }
 
-// -------------------------------------------------------------------- MLP forward
-__device__ __forceinline__ void load_params(const float* __restrict__ P, float* s)
-{
-    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) s[i] = P[i];
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(LT) k_mlp_forward(long long n, const float* __restrict__ feat,
-                                                    const float* __restrict__ params, float* __restrict__ out)
-{
-    __shared__ float sp[NPARAM];
-    load_params(params, sp);
-    for (long long i = (long long)blockIdx.x * LT + threadIdx.x; i < n; i += (long long)gridDim.x * LT) {
-        float f[NIN];
-#pragma unroll
-        for (int k = 0; k < NIN; k++) f[k] = feat[i * NIN + k];
-        float h1[NH];
-#pragma unroll
-        for (int o = 0; o < NH; o++) {
-            float z = sp[OFF_B1 + o];
-#pragma unroll
-            for (int k = 0; k < NIN; k++) z = fmaf(sp[OFF_W1 + o * NIN + k], f[k], z);
-            h1[o] = fmaxf(z, 0.f);
-        }
-        float y[NOUT];
-#pragma unroll
-        for (int k = 0; k < NOUT; k++) y[k] = sp[OFF_B3 + k];
-        for (int o = 0; o < NH; o++) {
-            float z = sp[OFF_B2 + o];
-#pragma unroll
-            for (int q = 0; q < NH; q++) z = fmaf(sp[OFF_W2 + o * NH + q], h1[q], z);
-            const float h2 = fmaxf(z, 0.f);
-#pragma unroll
-            for (int k = 0; k < NOUT; k++) y[k] = fmaf(sp[OFF_W3 + k * NH + o], h2, y[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < NOUT; k++) out[i * NOUT + k] = y[k];
-    }
-}
-
-// loss and dL/dout from the per-row statistics
-__global__ void k_spai_loss(long long n, const float* __restrict__ out, const float* __restrict__ G,
-                            const float* __restrict__ c, const float* __restrict__ d, const double* __restrict__ diag,
-                            const unsigned char* __restrict__ mask, double inv_npairs, float* __restrict__ gout,
-                            double* __restrict__ part)
-{
-    __shared__ double red[LT / 32];
-    double ls = 0.0;
-    for (long long i = (long long)blockIdx.x * LT + threadIdx.x; i < n; i += (long long)gridDim.x * LT) {
-        const float id = (float)(1.0 / diag[i]);
-        const unsigned char m = mask[i];
-        float p[7];
-#pragma unroll
-        for (int k = 0; k < 7; k++) p[k] = (m >> k) & 1 ? out[i * 7 + k] * id : 0.f;
-        float li = d[i];
-#pragma unroll
-        for (int k = 0; k < 7; k++) {
-            float gp = 0.f;
-#pragma unroll
-            for (int l = 0; l < 7; l++) gp = fmaf(G[i * 49 + k * 7 + l], p[l], gp);
-            const float ck = c[i * 7 + k];
-            li = fmaf(p[k], gp - 2.f * ck, li);
-            if (gout) gout[i * 7 + k] = (m >> k) & 1 ? 2.f * (gp - ck) * id * (float)inv_npairs : 0.f;
-        }
-        ls += (double)li;
-    }
-    ls = warp_sum(ls);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ls;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < LT / 32; w++) t += red[w];
-        part[blockIdx.x] = t * inv_npairs;
-    }
-}
-
-// -------------------------------------------------------------------- MLP backward
-// Tiles of BT rows: phase 1 (TPR threads per row, each an equal share of the hidden
-// units) recomputes the forward pass and writes
-// H1, H2, D2 = relu'(z2) * (W3^T gout), D1 = relu'(z1) * (W2^T D2) to shared memory;
-// phase 2 (all threads) accumulates the weight gradients as small dense products over
-// the tile (gW2 = D2^T H1, gW1 = D1^T F, gW3 = Gout^T H2, bias = column sums) in
-// registers; each block writes its partial gradient, a second kernel adds them in FP64.
-struct BwdSmem {
-    float p[NPARAM];
-    float H1[BT][NH + 1];
-    float H2[BT][NH + 1];
-    float D1[BT][NH + 1];
-    float D2[BT][NH + 1];
-    float F[BT][NIN];
-    float Go[BT][NOUT];
-};
-
-constexpr int BWD_THREADS = 512;
-constexpr int TPR = BWD_THREADS / BT;                            // threads per row in the row phase
-static_assert(BWD_THREADS == TPR * BT && NH % TPR == 0, "the row phase splits the hidden units evenly");
-constexpr int GPT = (NPARAM + BWD_THREADS - 1) / BWD_THREADS;   // gradient entries per thread (11)
-
-__global__ void __launch_bounds__(BWD_THREADS) k_mlp_backward(long long n, const float* __restrict__ feat,
-                                                              const float* __restrict__ params,
-                                                              const float* __restrict__ gout, float* __restrict__ gpart)
-{
-    extern __shared__ __align__(16) unsigned char bwd_raw[];
-    BwdSmem& s = *reinterpret_cast<BwdSmem*>(bwd_raw);
-    load_params(params, s.p);
-    float acc[GPT];
-#pragma unroll
-    for (int q = 0; q < GPT; q++) acc[q] = 0.f;
-    const long long ntiles = (n + BT - 1) / BT;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long i0 = t * BT;
-        __syncthreads();
-        // TPR threads per row, each taking an equal share of the hidden units of every
-        // layer (the same operations in the same order as one thread per row, so the
-        // same values)
-        {
-            const int rr = threadIdx.x % BT, hf = threadIdx.x / BT;
-            const int u0 = hf * (NH / TPR), u1 = u0 + NH / TPR;
-            const long long i = i0 + rr;
-            const bool valid = i < n;
-            float f[NIN], g[NOUT];
-#pragma unroll
-            for (int k = 0; k < NIN; k++) f[k] = valid ? feat[i * NIN + k] : 0.f;
-#pragma unroll
-            for (int k = 0; k < NOUT; k++) g[k] = valid ? gout[i * NOUT + k] : 0.f;
-            if (hf == 0) {
-#pragma unroll
-                for (int k = 0; k < NIN; k++) s.F[rr][k] = f[k];
-#pragma unroll
-                for (int k = 0; k < NOUT; k++) s.Go[rr][k] = g[k];
-            }
-            for (int o = u0; o < u1; o++) {
-                float z = s.p[OFF_B1 + o];
-#pragma unroll
-                for (int k = 0; k < NIN; k++) z = fmaf(s.p[OFF_W1 + o * NIN + k], f[k], z);
-                s.H1[rr][o] = valid ? fmaxf(z, 0.f) : 0.f;
-            }
-            __syncthreads();                                     // the row's whole H1
-            for (int o = u0; o < u1; o++) {
-                float z = s.p[OFF_B2 + o];
-                for (int q = 0; q < NH; q++) z = fmaf(s.p[OFF_W2 + o * NH + q], s.H1[rr][q], z);
-                float dz = 0.f;
-#pragma unroll
-                for (int k = 0; k < NOUT; k++) dz = fmaf(s.p[OFF_W3 + k * NH + o], g[k], dz);
-                s.H2[rr][o] = valid ? fmaxf(z, 0.f) : 0.f;
-                s.D2[rr][o] = (valid && z > 0.f) ? dz : 0.f;
-            }
-            __syncthreads();                                     // the row's whole D2
-            for (int q = u0; q < u1; q++) {
-                float dz = 0.f;
-                for (int o = 0; o < NH; o++) dz = fmaf(s.p[OFF_W2 + o * NH + q], s.D2[rr][o], dz);
-                s.D1[rr][q] = s.H1[rr][q] > 0.f ? dz : 0.f;
-            }
-        }
-        __syncthreads();
-        const int rows = (int)(n - i0 < BT ? n - i0 : BT);
-#pragma unroll
-        for (int q = 0; q < GPT; q++) {
-            const int idx = threadIdx.x + q * BWD_THREADS;
-            if (idx >= NPARAM) break;
-            float a = 0.f;
-            if (idx < OFF_B1) {                                  // W1[o][k] += D1[r][o] F[r][k]
-                const int o = idx / NIN, k = idx % NIN;
-                for (int r = 0; r < rows; r++) a = fmaf(s.D1[r][o], s.F[r][k], a);
-            } else if (idx < OFF_W2) {                           // b1
-                const int o = idx - OFF_B1;
-                for (int r = 0; r < rows; r++) a += s.D1[r][o];
-            } else if (idx < OFF_B2) {                           // W2[o][q] += D2[r][o] H1[r][q]
-                const int o = (idx - OFF_W2) / NH, qq = (idx - OFF_W2) % NH;
-                for (int r = 0; r < rows; r++) a = fmaf(s.D2[r][o], s.H1[r][qq], a);
-            } else if (idx < OFF_W3) {                           // b2
-                const int o = idx - OFF_B2;
-                for (int r = 0; r < rows; r++) a += s.D2[r][o];
-            } else if (idx < OFF_B3) {                           // W3[k][o] += Go[r][k] H2[r][o]
-                const int k = (idx - OFF_W3) / NH, o = (idx - OFF_W3) % NH;
-                for (int r = 0; r < rows; r++) a = fmaf(s.Go[r][k], s.H2[r][o], a);
-            } else {                                             // b3
-                const int k = idx - OFF_B3;
-                for (int r = 0; r < rows; r++) a += s.Go[r][k];
-            }
-            acc[q] += a;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < GPT; q++) {
-        const int idx = threadIdx.x + q * BWD_THREADS;
-        if (idx < NPARAM) gpart[(long long)blockIdx.x * NPARAM + idx] = acc[q];
-    }
-}
-
 __global__ void k_grad_reduce(const float* gpart, int nblk, double* grad)
 {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NPARAM; idx += gridDim.x * blockDim.x) {
@@ -360,10 +168,12 @@ struct cbg_spai {
     double* diag = nullptr;
     float *G = nullptr, *c = nullptr, *d = nullptr;
     double *e = nullptr, *r = nullptr, *part = nullptr;
-    float *master = nullptr, *bf = nullptr, *m1 = nullptr, *m2 = nullptr, *out = nullptr, *gout = nullptr;
-    float* gpart = nullptr;
+    float *master = nullptr, *bf = nullptr, *m1 = nullptr, *m2 = nullptr, *out = nullptr;
+    float* gpart = nullptr;       // per-CTA gradient partials of the network kernel
+    double* lpart = nullptr;      // per-CTA loss partials
     double* grad = nullptr;
-    int bwd_grid = 0;
+    int* fault = nullptr;         // a tensor-core wait ran out
+    int tc_grid = 0;
     long long npairs = 0;
     int step = 0;
 };
@@ -374,7 +184,7 @@ void free_spai(cbg_spai* s)
 {
     if (!s) return;
     void* ps[] = {s->rowptr, s->col, s->val, s->slot, s->mask, s->feat, s->diag, s->G, s->c, s->d, s->e, s->r,
-                  s->part, s->master, s->bf, s->m1, s->m2, s->out, s->gout, s->gpart, s->grad};
+                  s->part, s->master, s->bf, s->m1, s->m2, s->out, s->gpart, s->lpart, s->grad, s->fault};
     for (void* p : ps) cudaFree(p);
     delete s;
 }
@@ -414,20 +224,40 @@ void init_params(std::vector<float>& w, unsigned long long seed)
     w[OFF_B3 + 3] = 1.f;
 }
 
-int forward_and_loss(cbg_spai* s, double* loss, bool want_grad)
+MlpArgs net_args(const cbg_spai* s)
 {
-    const int g = grid_rows(s->n);
-    k_mlp_forward<<<g, LT, 0, s->stream>>>(s->n, s->feat, s->bf, s->out);
-    k_spai_loss<<<g, LT, 0, s->stream>>>(s->n, s->out, s->G, s->c, s->d, s->diag, s->mask,
-                                         1.0 / (double)std::max<long long>(1, s->npairs), want_grad ? s->gout : nullptr,
-                                         s->part);
-    std::vector<double> parts(g);
-    int rc = check(cudaMemcpyAsync(parts.data(), s->part, g * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    MlpArgs a{};
+    a.n = s->n;
+    a.feat = s->feat;
+    a.params = s->bf;
+    a.G = s->G;
+    a.c = s->c;
+    a.d = s->d;
+    a.diag = s->diag;
+    a.mask = s->mask;
+    a.inv_npairs = 1.0 / (double)std::max<long long>(1, s->npairs);
+    a.gpart = s->gpart;
+    a.lpart = s->lpart;
+    a.fault = s->fault;
+    return a;
+}
+
+// one fused pass of the network on the tensor cores: loss partials and the weight
+// gradient's per-CTA partials; with `loss`, the loss is read back (synchronising)
+int train_pass(cbg_spai* s, double* loss)
+{
+    int rc = check(mlp_tc_launch(MLP_TRAIN, s->tc_grid, s->stream, net_args(s)));
+    if (rc || !loss) return rc;
+    std::vector<double> parts(s->tc_grid);
+    int fault = 0;
+    rc = check(cudaMemcpyAsync(parts.data(), s->lpart, s->tc_grid * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (!rc) rc = check(cudaMemcpyAsync(&fault, s->fault, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     if (!rc) rc = check(cudaStreamSynchronize(s->stream));
     if (rc) return rc;
+    if (fault) return CBG_ERR_TIMEOUT;
     double t = 0.0;
     for (double v : parts) t += v;
-    if (loss) *loss = t;
+    *loss = t;
     return CBG_OK;
 }
 
@@ -455,24 +285,32 @@ int cbg_spai_create(const cbg_csr* A, int64_t sx, int64_t sxy, const cbg_options
             return rc;         \
         }                      \
     } while (0)
+    // per-row arrays of the network are padded to whole 128-row tiles (padding rows zero,
+    // diagonal one), so the tensor-core kernel stages full tiles
+    const long long np = (n + MLP_ROWS - 1) / MLP_ROWS * MLP_ROWS;
     TRY(alloc(&s->rowptr, n + 1)); TRY(alloc(&s->col, nnz)); TRY(alloc(&s->val, nnz));
     const cudaMemcpyKind k = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     TRY(check(cudaMemcpy(s->rowptr, A->row_ptr, (n + 1) * sizeof(int), k)));
     TRY(check(cudaMemcpy(s->col, A->col, nnz * sizeof(int), k)));
     TRY(check(cudaMemcpy(s->val, A->val, nnz * sizeof(double), k)));
-    TRY(alloc(&s->slot, nnz)); TRY(alloc(&s->mask, n)); TRY(alloc(&s->feat, n * NIN)); TRY(alloc(&s->diag, n));
-    TRY(alloc(&s->G, n * 49)); TRY(alloc(&s->c, n * 7)); TRY(alloc(&s->d, n));
+    TRY(alloc(&s->slot, nnz)); TRY(alloc(&s->mask, np)); TRY(alloc(&s->feat, np * NIN)); TRY(alloc(&s->diag, np));
+    TRY(alloc(&s->G, np * 49)); TRY(alloc(&s->c, np * 7)); TRY(alloc(&s->d, np));
     TRY(alloc(&s->e, n)); TRY(alloc(&s->r, n)); TRY(alloc(&s->part, 4096));
     TRY(alloc(&s->master, NPARAM)); TRY(alloc(&s->bf, NPARAM)); TRY(alloc(&s->m1, NPARAM)); TRY(alloc(&s->m2, NPARAM));
-    TRY(alloc(&s->out, n * NOUT)); TRY(alloc(&s->gout, n * NOUT)); TRY(alloc(&s->grad, NPARAM));
-    int sms = 1, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s->bwd_grid = (int)std::max<long long>(1, std::min<long long>((n + BT - 1) / BT, (long long)sms));
-    TRY(alloc(&s->gpart, (size_t)s->bwd_grid * NPARAM));
-    TRY(check(cudaMemset(s->G, 0, n * 49 * sizeof(float))));
-    TRY(check(cudaMemset(s->c, 0, n * 7 * sizeof(float))));
-    TRY(check(cudaMemset(s->d, 0, n * sizeof(float))));
+    TRY(alloc(&s->out, np * NOUT)); TRY(alloc(&s->grad, NPARAM)); TRY(alloc(&s->fault, 1));
+    s->tc_grid = mlp_tc_grid(n);
+    TRY(alloc(&s->gpart, (size_t)s->tc_grid * NPARAM));
+    TRY(alloc(&s->lpart, (size_t)s->tc_grid));
+    TRY(check(cudaMemset(s->G, 0, np * 49 * sizeof(float))));
+    TRY(check(cudaMemset(s->c, 0, np * 7 * sizeof(float))));
+    TRY(check(cudaMemset(s->d, 0, np * sizeof(float))));
+    TRY(check(cudaMemset(s->mask, 0, np)));
+    TRY(check(cudaMemset(s->feat, 0, np * NIN * sizeof(float))));
+    TRY(check(cudaMemset(s->fault, 0, sizeof(int))));
+    if (np > n) {
+        std::vector<double> ones(np - n, 1.0);
+        TRY(check(cudaMemcpy(s->diag + n, ones.data(), (np - n) * sizeof(double), cudaMemcpyHostToDevice)));
+    }
     TRY(check(cudaMemset(s->m1, 0, NPARAM * sizeof(float))));
     TRY(check(cudaMemset(s->m2, 0, NPARAM * sizeof(float))));
     int* bad = reinterpret_cast<int*>(s->part);
@@ -485,7 +323,6 @@ int cbg_spai_create(const cbg_csr* A, int64_t sx, int64_t sxy, const cbg_options
     init_params(w, 20201201ull);
     TRY(check(cudaMemcpy(s->master, w.data(), NPARAM * sizeof(float), cudaMemcpyHostToDevice)));
     k_round_bf16<<<32, 256>>>(s->master, s->bf);
-    TRY(check(cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem))));
     TRY(check(cudaDeviceSynchronize()));
 #undef TRY
     *out = s;
@@ -507,7 +344,7 @@ int cbg_spai_add_pair(cbg_spai* s, const double* xstar, const double* xk)
 int cbg_spai_loss(cbg_spai* s, double* loss)
 {
     if (!s || !loss || s->npairs < 1) return CBG_ERR_ARG;
-    return forward_and_loss(s, loss, false);
+    return train_pass(s, loss);
 }
 
 int cbg_spai_train(cbg_spai* s, int steps, double lr, double* loss_first, double* loss_last)
@@ -515,18 +352,17 @@ int cbg_spai_train(cbg_spai* s, int steps, double lr, double* loss_first, double
     if (!s || steps < 0 || !(lr > 0.0) || s->npairs < 1) return CBG_ERR_ARG;
     double l0 = 0.0, l = 0.0;
     for (int it = 0; it < steps; it++) {
-        int rc = forward_and_loss(s, &l, true);
+        // the loss is read back once, before the first update (no per-step synchronisation)
+        int rc = train_pass(s, it == 0 ? &l0 : nullptr);
         if (rc) return rc;
-        if (it == 0) l0 = l;
-        k_mlp_backward<<<s->bwd_grid, BWD_THREADS, sizeof(BwdSmem), s->stream>>>(s->n, s->feat, s->bf, s->gout, s->gpart);
-        k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->gpart, s->bwd_grid, s->grad);
+        k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->gpart, s->tc_grid, s->grad);
         s->step++;
         k_adam<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->master, s->bf, s->grad, s->m1, s->m2, s->step,
                                                             (float)lr, 0.9f, 0.999f, 1e-8f);
         rc = check(cudaGetLastError());
         if (rc) return rc;
     }
-    int rc = forward_and_loss(s, &l, false);
+    int rc = train_pass(s, &l);                           // the loss after the last update
     if (rc) return rc;
     if (steps == 0) l0 = l;
     if (loss_first) *loss_first = l0;
@@ -538,9 +374,12 @@ int cbg_spai_values(cbg_spai* s, double* pvals)
 {
     if (!s || !pvals) return CBG_ERR_ARG;
     const int g = grid_rows(s->n);
-    k_mlp_forward<<<g, LT, 0, s->stream>>>(s->n, s->feat, s->bf, s->out);
+    MlpArgs a = net_args(s);
+    a.out = s->out;
+    int rc = check(mlp_tc_launch(MLP_FWD, s->tc_grid, s->stream, a));
+    if (rc) return rc;
     k_spai_pvals<<<g, LT, 0, s->stream>>>(s->rowptr, s->slot, s->n, s->out, s->diag, pvals);
-    int rc = check(cudaGetLastError());
+    rc = check(cudaGetLastError());
     if (!rc) rc = check(cudaStreamSynchronize(s->stream));
     return rc;
 }
@@ -565,52 +404,77 @@ void cbg_spai_destroy(cbg_spai* s)
     free_spai(s);
 }
 
-// ---- test access: one forward / backward with given FP32 parameters (rounded to BF16)
+// ---- test access: one forward / backward with given FP32 parameters (rounded to BF16),
+// on the tensor-core kernel
 int cbg_mlp_forward(int64_t rows, const float* feat, const float* params_host, float* out, void* stream)
 {
-    if (rows < 1 || !feat || !params_host || !out) return CBG_ERR_ARG;
+    if (rows < 1 || !feat || !params_host || !out || ((uintptr_t)feat & 15)) return CBG_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     float *m = nullptr, *b = nullptr;
+    int* fault = nullptr;
     int rc = alloc(&m, NPARAM);
     if (!rc) rc = alloc(&b, NPARAM);
+    if (!rc) rc = alloc(&fault, 1);
+    if (!rc) rc = check(cudaMemsetAsync(fault, 0, sizeof(int), st));
     if (!rc) rc = check(cudaMemcpyAsync(m, params_host, NPARAM * sizeof(float), cudaMemcpyHostToDevice, st));
     if (!rc) {
         k_round_bf16<<<32, 256, 0, st>>>(m, b);
-        k_mlp_forward<<<grid_rows(rows), LT, 0, st>>>(rows, feat, b, out);
-        rc = check(cudaGetLastError());
+        MlpArgs a{};
+        a.n = rows;
+        a.feat = feat;
+        a.params = b;
+        a.out = out;
+        a.fault = fault;
+        rc = check(mlp_tc_launch(MLP_FWD, mlp_tc_grid(rows), st, a));
+        int hf = 0;
+        if (!rc) rc = check(cudaMemcpyAsync(&hf, fault, sizeof(int), cudaMemcpyDeviceToHost, st));
         if (!rc) rc = check(cudaStreamSynchronize(st));
+        if (!rc && hf) rc = CBG_ERR_TIMEOUT;
     }
     cudaFree(m);
     cudaFree(b);
+    cudaFree(fault);
     return rc;
 }
 
 int cbg_mlp_backward(int64_t rows, const float* feat, const float* params_host, const float* gout, double* grad_host,
                      void* stream)
 {
-    if (rows < 1 || !feat || !params_host || !gout || !grad_host) return CBG_ERR_ARG;
+    if (rows < 1 || !feat || !params_host || !gout || !grad_host || ((uintptr_t)feat & 15) || ((uintptr_t)gout & 15))
+        return CBG_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    int sms = 1, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::max<long long>(1, std::min<long long>((rows + BT - 1) / BT, sms));
+    const int grid = mlp_tc_grid(rows);
     float *m = nullptr, *b = nullptr, *gp = nullptr;
     double* g = nullptr;
+    int* fault = nullptr;
     int rc = alloc(&m, NPARAM);
     if (!rc) rc = alloc(&b, NPARAM);
     if (!rc) rc = alloc(&gp, (size_t)grid * NPARAM);
     if (!rc) rc = alloc(&g, NPARAM);
-    if (!rc) rc = check(cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)));
+    if (!rc) rc = alloc(&fault, 1);
+    if (!rc) rc = check(cudaMemsetAsync(fault, 0, sizeof(int), st));
     if (!rc) rc = check(cudaMemcpyAsync(m, params_host, NPARAM * sizeof(float), cudaMemcpyHostToDevice, st));
     if (!rc) {
         k_round_bf16<<<32, 256, 0, st>>>(m, b);
-        k_mlp_backward<<<grid, BWD_THREADS, sizeof(BwdSmem), st>>>(rows, feat, b, gout, gp);
-        k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(gp, grid, g);
-        rc = check(cudaGetLastError());
+        MlpArgs a{};
+        a.n = rows;
+        a.feat = feat;
+        a.params = b;
+        a.gout = gout;
+        a.gpart = gp;
+        a.fault = fault;
+        rc = check(mlp_tc_launch(MLP_BWD, grid, st, a));
+        if (!rc) {
+            k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(gp, grid, g);
+            rc = check(cudaGetLastError());
+        }
+        int hf = 0;
         if (!rc) rc = check(cudaMemcpyAsync(grad_host, g, NPARAM * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (!rc) rc = check(cudaMemcpyAsync(&hf, fault, sizeof(int), cudaMemcpyDeviceToHost, st));
         if (!rc) rc = check(cudaStreamSynchronize(st));
+        if (!rc && hf) rc = CBG_ERR_TIMEOUT;
     }
-    cudaFree(m); cudaFree(b); cudaFree(gp); cudaFree(g);
+    cudaFree(m); cudaFree(b); cudaFree(gp); cudaFree(g); cudaFree(fault);
     return rc;
 }
 

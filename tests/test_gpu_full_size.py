@@ -78,7 +78,8 @@ def test_batch512_full_size(fmt):
 def test_learned96_full_size():
     """Diffusion 96^3 (n = 884,736) with a lognormal(0, 1) field: pairs from FP64 GMRES and
     400 training steps as bench.py runs them; the learned operator at 2,000 sampled rows
-    against the oracle's FP64 network on the same BF16-rounded weights; the SPAI-
+    against the oracle's FP64 network on the same BF16-rounded weights (within 2e-2 of
+    the outputs' scale: the network computes with BF16 activations); the SPAI-
     preconditioned f32-basis solve reaches the 1e-10 true residual in fewer steps than no
     preconditioner."""
     torch, cb = need_gpu()
@@ -115,7 +116,7 @@ def test_learned96_full_size():
     for t, i in enumerate(rows):
         for q in range(A.rowptr[i], A.rowptr[i + 1]):
             got = pv[q] * diag[i]
-            assert abs(got - ref[t, slot[q]]) <= 1e-5 * max(1.0, np.max(np.abs(ref))), (i, q)
+            assert abs(got - ref[t, slot[q]]) <= 2e-2 * max(1.0, np.max(np.abs(ref))), (i, q)
     bd = to_dev(torch, b)
     its = {}
     for pc in ("none", "spai"):
