@@ -368,6 +368,7 @@ def run_batch(args):
             sched[f] = tuple(args.schedule)
         else:
             sched[f] = solvers[f].tune(bd, x, tol=tol, cache_path=cache)
+        sched[f] = tuple(sched[f]) + (solvers[f].spmv_lanes(),)
     for _ in range(args.warmup):
         for f in fmts:
             x.zero_(); solvers[f].solve(bd, x, tol=tol)
@@ -442,7 +443,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD.replace("batch512", f"batch{len(mats)}"), "nsys": len(mats),
                    "total_rows": int(b.size), "restart": m,
-                   "tol": tol, "formats": fmts, "schedule_cluster_split": {f: list(v) for f, v in sched.items()},
+                   "tol": tol, "formats": fmts, "schedule_cluster_split_lanes": {f: list(v) for f, v in sched.items()},
                    "value_is": "time(f64 basis) / time(f32 basis), whole batch in one persistent launch",
                    "l2": "no flush: basis of the batch (0.5-2 GB) exceeds the 129 MB L2"},
         "time_to_solution_s": {f: round(v / 1000, 4) for f, v in t.items()},

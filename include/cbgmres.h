@@ -4,7 +4,8 @@
  * Method: Aliaga, Anzt, Gruetzmacher, Quintana-Orti, Tomas, "Compressed Basis GMRES on
  * High Performance GPUs" (arXiv 2009.12101).  Restarted, right-preconditioned GMRES(m)
  * (Fig. 1) whose Krylov basis V is stored in a compact format while the arithmetic
- * keeps FP64 accuracy (Section 3); the basis is decompressed on every read and
+ * works at FP64 class accuracy (Section 3: native FP64, or by default double-float
+ * FP32 pairs with about 47-bit operations, see cbg_arith); the basis is decompressed on every read and
  * compressed on every store (the memory accessor of Section 4.2); fixed-point formats carry
  * the per-vector scale sigma_j = (||v_j||_inf / ||v_j||_2) / max_intxx (Section 4.2);
  * convergence ||b - A x||_2 <= tau ||b||_2 is confirmed by an explicit residual each
@@ -70,8 +71,14 @@ typedef enum { CBG_ORTHO_CGS = 0, CBG_ORTHO_MGS = 1 } cbg_ortho;
 /* Arithmetic of the basis products (the CGS projection, its re-orthogonalisation and
  * the solution update of Fig. 1) and of the per-step SpMV.
  * CBG_ARITH_DF32: products and partial sums in double-float (pairs of FP32 with
- *   error-free transformations, >= 44-bit effective significand per partial chain),
- *   cross-thread and cross-block combination in FP64.  The per-step SpMV forms each
+ *   error-free transformations), cross-thread and cross-block combination in FP64.
+ *   Accuracy: each product and sum is carried to about 2^-46 relative (FP64: 2^-53), so
+ *   the error bounds of the basis products and of the SpMV rows are those of FP64 with
+ *   the unit roundoff 2^-46 in place of 2^-53: 2^6 - 2^8 looser than the same sums in
+ *   native FP64, 2^20 tighter than FP32.  The basis dot sums each thread's chain of
+ *   about n / 38,912 products in double-float and the chains in FP64, so its bound,
+ *   about (n / 38,912) 2^-46 sum |v_i w_i|, stays below FP64's recursive-summation
+ *   bound n 2^-53 sum |v_i w_i| for every n >= 128.  The per-step SpMV forms each
  *   product val * x exactly as an FP32 pair from the values split once into FP32 hi / lo
  *   planes (a relative 2^-48 perturbation of A) and delivers w as such planes.  The
  *   per-step operator (A, or A D^{-1} under Jacobi) is normalised by a power of two so
@@ -117,7 +124,10 @@ typedef struct {
     int32_t reorth;          /* cbg_reorth, default CBG_REORTH_ALWAYS (CGS + 1 pass)   */
     int32_t precond;         /* cbg_precond, default CBG_PC_NONE                       */
     int32_t arith;           /* cbg_arith, default CBG_ARITH_DF32                      */
-    int32_t spmv_group;      /* lanes per CSR row: 0 = automatic, else 1..32 (pow2)   */
+    int32_t spmv_group;      /* lanes per CSR row: 0 = automatic, else 1..32 (pow2):   *
+                              * automatic times 1, 2, .., 32 lanes at create on       *
+                              * matrices of >= 65536 rows and keeps the fastest, and  *
+                              * picks by nonzeros per row below that                  */
     double eta;              /* conditional re-orthogonalisation threshold (1/sqrt 2)  */
     double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
     void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
@@ -246,10 +256,11 @@ int cbg_basis_dot(int fmt, int arith, int64_t n, int ncols, const void* V, int64
 int cbg_basis_axpy(int fmt, int arith, int64_t n, int ncols, const void* V, int64_t ld,
                    const double* scales, const double* h, double* w, void* stream);
 
-/* ---- multi-RHS basis product: H = V^T W for k <= 8 vectors sharing one basis -------
+/* ---- multi-RHS basis product: H = V^T W for k <= 64 vectors sharing one basis ------
  * No counterpart in the paper (its GMRES has one right-hand side); the building block of
- * block Krylov orthogonalisation.  Reads V once for all k vectors (one split-K product
- * in double-float arithmetic, like cbg_basis_dot with arith = CBG_ARITH_DF32).
+ * block Krylov orthogonalisation.  Vectors are taken in groups of 8 (the last may be
+ * smaller); each group reads V once for all its vectors (one split-K product in
+ * double-float arithmetic, like cbg_basis_dot with arith = CBG_ARITH_DF32).
  *   V: device codes of format fmt, ncols (<= 320) columns of leading dimension ld
  *      elements (ld >= n, ld % 4096 == 0, rows n..ld-1 zero);
  *   scales[ncols]: device decode factors;  W: device, n x k column-major, leading
@@ -274,6 +285,9 @@ int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld
 int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
                              int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                              void* stream, int path);
+
+/* Lanes per CSR row of the handle's SpMV (the tuned or given schedule), or CBG_ERR_ARG. */
+int cbgmres_spmv_group(const cbg_handle* h);
 
 /* Test of the failure path (no counterpart in the paper).  The next `dots` launches of
  * the pipelined basis dot (DF32 arithmetic) made by solves on h withhold their first
@@ -335,13 +349,20 @@ int cbgmres_create_batched(int nsys, const cbg_csr* As, int restart, int fmt,
 int cbgmres_solve_batched(cbg_batch* bt, const double* b, double* x, double tol, int64_t maxit,
                           cbg_stats* per_sys);
 /* Autotuner: time every feasible schedule (cluster size 1..16, split threshold) on this
- * problem (x restored to x0 before each trial) and keep the fastest; cache_path (may be
- * NULL) is a JSON-lines file consulted first and appended to, keyed by GPU, format,
- * restart length, system count and total rows.  The chosen schedule is returned. */
+ * problem (x restored to x0 before each trial) with a thread per SpMV row, then the
+ * SpMV's lanes per row (2, 4, 8: the lanes of a row split its nonzeros) for the best of
+ * them, and keep the fastest; cache_path (may be NULL) is a JSON-lines file consulted
+ * first and appended to, keyed by GPU, format, restart length, system count and total
+ * rows.  The chosen cluster size and split threshold are returned
+ * (cbgmres_batched_spmv_lanes(bt, 0) reports the lanes). */
 int cbgmres_tune_batched(cbg_batch* bt, const double* b, double* x, double tol, int64_t maxit,
                          const char* cache_path, int* cluster_out, int* split_rows_out);
 /* Set the schedule explicitly (cluster size a power of two <= 16). */
 int cbgmres_batched_schedule(cbg_batch* bt, int cluster, int split_rows);
+/* SpMV lanes per row of the batched kernel: lanes = 1 (a thread per row, four rows in
+ * flight), 2, 4 or 8 sets it; lanes = 0 only queries.  Returns the lanes in use, or
+ * CBG_ERR_ARG. */
+int cbgmres_batched_spmv_lanes(cbg_batch* bt, int lanes);
 void cbgmres_destroy_batched(cbg_batch* bt);
 
 /* Try the handles in order (e.g. learned SPAI, Jacobi, none -- all for the same A),

@@ -104,6 +104,7 @@ def lib():
             L.cbgmres_spmv.argtypes = [vp, vp, vp]
             L.cbgmres_profile.argtypes = [vp, C.POINTER(Profile), i32]
             L.cbgmres_test_stall.argtypes = [vp, i32, C.c_int64]
+            L.cbgmres_spmv_group.argtypes = [vp]
             L.cbgmres_destroy.argtypes = [vp]
             L.cbgmres_destroy.restype = None
             L.cbg_encode.argtypes = [i32, i64, vp, d, vp, C.POINTER(d), vp]
@@ -121,6 +122,7 @@ def lib():
             L.cbgmres_tune_batched.argtypes = [vp, vp, vp, d, i64, C.c_char_p, C.POINTER(C.c_int),
                                                C.POINTER(C.c_int)]
             L.cbgmres_batched_schedule.argtypes = [vp, i32, i32]
+            L.cbgmres_batched_spmv_lanes.argtypes = [vp, i32]
             L.cbgmres_solve_fallback.argtypes = [vp, i32, vp, vp, d, i64, C.POINTER(Stats), C.POINTER(C.c_int)]
             L.cbg_spai_create.argtypes = [C.POINTER(Csr), i64, i64, C.POINTER(Options), C.POINTER(vp)]
             L.cbg_spai_add_pair.argtypes = [vp, vp, vp]
@@ -308,6 +310,10 @@ class Solver:
         return {c: {"ms": p.ms[i], "bytes": p.bytes[i], "launches": p.launches[i]}
                 for i, c in enumerate(PROFILE_CLASSES)}
 
+    def spmv_group(self) -> int:
+        """Lanes per CSR row of this handle's SpMV (tuned at create on large matrices)."""
+        return _check(lib().cbgmres_spmv_group(self._h), "cbgmres_spmv_group")
+
     def test_stall(self, dots: int = 1, wait_cycles: int = 2_000_000):
         """Failure-path test: the next `dots` pipelined dot launches withhold their first
         bulk-copy stage and give up their waits after `wait_cycles` clock cycles."""
@@ -369,7 +375,7 @@ def basis_dot_noalloc(fmt: str, arith: str, n: int, V, ld: int, scales, w, strea
 
 def basis_dot_multi(fmt: str, n: int, V, ld: int, scales, W, stream=None, workspace=None, path: str = "auto",
                     out=None):
-    """H = V^T W for k <= 8 vectors; V: code matrix (ncols x ld codes); W: CUDA float64
+    """H = V^T W for k <= 64 vectors; V: code matrix (ncols x ld codes); W: CUDA float64
     tensor (k, ldw) whose row r holds vector r.  scales: host array or CUDA float64 tensor
     of the ncols decode factors.  Returns H (CUDA tensor, ncols x k; `out` if given)."""
     torch = _torch()
@@ -466,6 +472,10 @@ class BatchedSolver:
 
     def schedule(self, cluster: int, split_rows: int):
         _check(lib().cbgmres_batched_schedule(self._h, cluster, split_rows), "cbgmres_batched_schedule")
+
+    def spmv_lanes(self, lanes: int = 0) -> int:
+        """SpMV lanes per row (1, 2, 4, 8); 0 only queries."""
+        return _check(lib().cbgmres_batched_spmv_lanes(self._h, int(lanes)), "cbgmres_batched_spmv_lanes")
 
 
 def solve_fallback(solvers, b, x, tol: float = 1e-10, maxit: int = 100000):

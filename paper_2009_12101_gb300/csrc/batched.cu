@@ -32,6 +32,7 @@ namespace {
 struct Schedule {
     int cluster = 1;
     int split_rows = 1 << 30;
+    int lanes = 1;           // SpMV lanes per row (1: a thread per row)
 };
 
 template <int F> struct BOps {
@@ -183,6 +184,7 @@ BatchArgs make_args(const cbg_batch* bt, const Schedule& sc, double tol, long lo
     a.eps_bd = bt->opt.breakdown_eps;
     a.split_rows = sc.split_rows;
     a.max_rows_block = 0;
+    a.spmv_lanes = sc.lanes;
     return a;
 }
 
@@ -213,7 +215,8 @@ int enqueue(cbg_batch* bt, const Schedule& sc, int grid, size_t sm, double tol, 
 int run_graph(cbg_batch* bt, double tol, long long maxit)
 {
     const bool stale = !bt->have_graph || bt->graph_sched.cluster != bt->sched.cluster ||
-                       bt->graph_sched.split_rows != bt->sched.split_rows || bt->graph_tol != tol ||
+                       bt->graph_sched.split_rows != bt->sched.split_rows ||
+                       bt->graph_sched.lanes != bt->sched.lanes || bt->graph_tol != tol ||
                        bt->graph_maxit != maxit;
     if (stale) {
         if (bt->graph) cudaGraphExecDestroy(bt->graph);
@@ -264,7 +267,7 @@ bool cache_lookup(const char* path, const std::string& key, Schedule* out)
     std::string line;
     bool found = false;
     while (std::getline(f, line)) {
-        // {"key": "...", "cluster": C, "split_rows": S}
+        // {"key": "...", "cluster": C, "split_rows": S, "lanes": L}
         auto kp = line.find("\"key\": \"");
         if (kp == std::string::npos) continue;
         auto ke = line.find('"', kp + 8);
@@ -275,9 +278,12 @@ bool cache_lookup(const char* path, const std::string& key, Schedule* out)
         if (cp == std::string::npos || sp == std::string::npos) continue;
         c = std::atoi(line.c_str() + cp + 11);
         s = std::atoi(line.c_str() + sp + 14);
-        if (c >= 1 && s >= 1) {
+        auto lp = line.find("\"lanes\": ");
+        const int l = lp == std::string::npos ? 1 : std::atoi(line.c_str() + lp + 9);
+        if (c >= 1 && s >= 1 && (l == 1 || l == 2 || l == 4 || l == 8)) {
             out->cluster = c;
             out->split_rows = s;
+            out->lanes = l;
             found = true;   // the last entry for a key wins
         }
     }
@@ -289,7 +295,7 @@ void cache_store(const char* path, const std::string& key, const Schedule& sc, d
     if (!path) return;
     std::ofstream f(path, std::ios::app);
     f << "{\"key\": \"" << key << "\", \"cluster\": " << sc.cluster << ", \"split_rows\": " << sc.split_rows
-      << ", \"ms\": " << ms << "}\n";
+      << ", \"lanes\": " << sc.lanes << ", \"ms\": " << ms << "}\n";
 }
 
 }  // namespace
@@ -503,17 +509,26 @@ int cbgmres_tune_batched(cbg_batch* bt, const double* b, double* x, double tol, 
         double best_ms = 1e300;
         bt->h_io[0] = const_cast<double*>(b);
         bt->h_io[1] = x;
-        for (const Schedule& t : cands) {
+        auto trial = [&](const Schedule& t) {
             const size_t sm = smem_bytes(bt, t);
             const int grid = grid_for(bt, t, sm);
             cudaMemcpyAsync(x, x0, bt->total_rows * sizeof(double), cudaMemcpyDeviceToDevice, bt->stream);
             cudaEventRecord(bt->e0, bt->stream);
             int rc = enqueue(bt, t, grid, sm, tol, maxit, bt->stream);
             cudaEventRecord(bt->e1, bt->stream);
-            if (rc || cudaEventSynchronize(bt->e1) != cudaSuccess) { cudaGetLastError(); continue; }
+            if (rc || cudaEventSynchronize(bt->e1) != cudaSuccess) { cudaGetLastError(); return; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, bt->e0, bt->e1);
             if (ms < best_ms) { best_ms = ms; best = t; }
+        };
+        // cluster size and split threshold with a thread per SpMV row, then the SpMV's
+        // lanes per row for the best of those
+        for (const Schedule& t : cands) trial(t);
+        const Schedule first = best;
+        for (int l : {2, 4, 8}) {
+            Schedule t = first;
+            t.lanes = l;
+            trial(t);
         }
         cudaFree(x0);
         if (best_ms >= 1e300) return CBG_ERR_CUDA;
@@ -528,10 +543,17 @@ int cbgmres_tune_batched(cbg_batch* bt, const double* b, double* x, double tol, 
 int cbgmres_batched_schedule(cbg_batch* bt, int cluster, int split_rows)
 {
     if (!bt || cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) || split_rows < 1) return CBG_ERR_ARG;
-    Schedule t{cluster, split_rows};
+    Schedule t{cluster, split_rows, bt->sched.lanes};
     if (grid_for(bt, t, smem_bytes(bt, t)) <= 0) return CBG_ERR_UNSUPPORTED;
     bt->sched = t;
     return CBG_OK;
+}
+
+int cbgmres_batched_spmv_lanes(cbg_batch* bt, int lanes)
+{
+    if (!bt || lanes < 0 || lanes > 8 || (lanes & (lanes - 1))) return CBG_ERR_ARG;
+    if (lanes > 0) bt->sched.lanes = lanes;
+    return bt->sched.lanes;
 }
 
 void cbgmres_destroy_batched(cbg_batch* bt)

@@ -66,6 +66,8 @@ struct BatchArgs {
     double eps_bd;
     int split_rows;
     int max_rows_block;     // capacity of the shared-memory w (rows)
+    int spmv_lanes;         // SpMV schedule: 1 = a thread per row (4 rows in flight), or 2, 4, 8
+                            // lanes per row (the lanes split the row's nonzeros)
 };
 
 // shared-memory layout of one block (dynamic)
@@ -264,6 +266,101 @@ template <int FMT> struct BatchedSolver {
         return df_to_double(ssS, ssC);
     }
 
+    // The SpMVs above with L = a.spmv_lanes lanes per row (L = 2, 4, 8): the lanes of a
+    // group take every L-th nonzero of the row and their partial sums meet in shuffles.
+    // Groups walk the block's rows in warp-uniform passes, so every shuffle has the whole
+    // warp.  Same results up to the order of each row's sum.
+    template <bool CODES>
+    static __device__ double spmv_lanes(const BatchArgs& a, const BatchSys& s, BtSmem* sm, int r0, int r1,
+                                        const void* x, double xscale, const double* vals, bool residual)
+    {
+        const int* rp = a.rowptr + s.rp_off;
+        const int* ci = a.col + s.nz_off;
+        const double* va = vals + s.nz_off;
+        const double* bb = a.io[0] + s.vec_off;
+        const int L = a.spmv_lanes, lg = threadIdx.x & (L - 1), gpw = 32 / L;
+        const int gw = (threadIdx.x & 31) / L, warp = threadIdx.x >> 5;
+        double ss = 0.0;
+        for (int base = r0 + warp * gpw; base < r1; base += (BT_THREADS / 32) * gpw) {
+            const int r = base + gw;
+            const bool valid = r < r1;
+            double t = 0.0;
+            if (valid) {
+                const int p1 = rp[r + 1];
+                for (int p = rp[r] + lg; p < p1; p += L) {
+                    double xv;
+                    if constexpr (CODES) xv = code_value<FMT>(x, ci[p]);
+                    else xv = reinterpret_cast<const double*>(x)[ci[p]];
+                    t = __fma_rn(va[p], xv, t);
+                }
+            }
+            for (int o = L >> 1; o > 0; o >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
+            if (valid && lg == 0) {
+                double v = t;
+                if constexpr (CODES) v = __dmul_rn(v, xscale);
+                if (residual) v = __dsub_rn(bb[r], v);
+                float hi, lo;
+                split_f64(v, hi, lo);
+                sm->ws[r - r0] = make_float2(hi, lo);
+                ss = __fma_rn(v, v, ss);
+            }
+        }
+        return ss;
+    }
+
+    static __device__ double spmv_df_lanes(const BatchArgs& a, const BatchSys& s, BtSmem* sm, int r0, int r1,
+                                           const void* x, double xscale)
+    {
+        const int* rp = a.rowptr + s.rp_off;
+        const int* ci = a.col + s.nz_off;
+        const float* vh = a.valpdf + s.nz_off;
+        const float* vl = a.valpdf + a.nnz_all + s.nz_off;
+        const bool xsplit = xscale != 1.0;
+        float xsh = 1.f, xsl = 0.f;
+        if (xsplit) split_f64(xscale, xsh, xsl);
+        const int L = a.spmv_lanes, lg = threadIdx.x & (L - 1), gpw = 32 / L;
+        const int gw = (threadIdx.x & 31) / L, warp = threadIdx.x >> 5;
+        float ssS = 0.f, ssC = 0.f;
+        for (int base = r0 + warp * gpw; base < r1; base += (BT_THREADS / 32) * gpw) {
+            const int r = base + gw;
+            const bool valid = r < r1;
+            float S = 0.f, C = 0.f;
+            if (valid) {
+                const int p1 = rp[r + 1];
+                for (int p = rp[r] + lg; p < p1; p += L) {
+                    float xh, xl;
+                    xval_df<FMT>(x, ci[p], xh, xl);
+                    if constexpr (SingleFloat<FMT>::value) df_mac(S, C, xh, vh[p], vl[p]);
+                    else df_mac2(S, C, xh, xl, vh[p], vl[p]);
+                }
+            }
+            for (int o = L >> 1; o > 0; o >>= 1) {
+                const float S2 = __shfl_xor_sync(0xffffffffu, S, o), C2 = __shfl_xor_sync(0xffffffffu, C, o);
+                df_add(S, C, S2, C2);
+            }
+            if (valid && lg == 0) {
+                float hi, lo;
+                two_sum(S, C, hi, lo);
+                if (xsplit) {
+                    const float p = __fmul_rn(hi, xsh);
+                    float e = __fmaf_rn(hi, xsh, -p);
+                    e = __fmaf_rn(hi, xsl, e);
+                    e = __fmaf_rn(lo, xsh, e);
+                    two_sum(p, e, hi, lo);
+                }
+                sm->ws[r - r0] = make_float2(hi, lo);
+                const float p = __fmul_rn(hi, hi);
+                float e = __fmaf_rn(hi, hi, -p);
+                e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
+                float t, te;
+                two_sum(ssS, p, t, te);
+                ssC = __fadd_rn(ssC, __fadd_rn(te, e));
+                ssS = t;
+            }
+        }
+        return df_to_double(ssS, ssC);
+    }
+
     // partial h_k = sum over own rows of dec(V_k) w, k < ncols, into sm->red[0..ncols)
     // (scale applied); one warp per column, lanes walk the rows in 16-byte chunks.
     static __device__ void dot(const BatchArgs& a, const BatchSys& s, BtSmem* sm, int r0, int r1, int ncols)
@@ -421,7 +518,8 @@ template <int FMT> struct BatchedSolver {
                 // residual r = b - A x into ws; beta, ||r||_inf
                 team.sync();                                   // x of all blocks visible
                 double v[2];
-                v[0] = spmv<false>(a, s, sm, r0, r1, x, 1.0, a.val, true);
+                v[0] = a.spmv_lanes > 1 ? spmv_lanes<false>(a, s, sm, r0, r1, x, 1.0, a.val, true)
+                                        : spmv<false>(a, s, sm, r0, r1, x, 1.0, a.val, true);
                 v[1] = 0.0;
                 double mxl = 0.0;
                 for (int r = r0 + threadIdx.x; r < r1; r += BT_THREADS) {
@@ -474,10 +572,13 @@ template <int FMT> struct BatchedSolver {
                     // splitting every gathered code.
                     double om[1];
                     const unsigned char* vj = a.V + s.v_off + (long long)j * s.ld * BS;
-                    if (FMT != F64 && a.valpdf)
-                        om[0] = spmv_df(a, s, sm, r0, r1, vj, sm->scale[j]);   // planes hold 2^s A_pc
+                    const double xs = __dmul_rn(sm->scale[j], s.pscale);
+                    if (FMT != F64 && a.valpdf)                  // planes hold 2^s A_pc
+                        om[0] = a.spmv_lanes > 1 ? spmv_df_lanes(a, s, sm, r0, r1, vj, sm->scale[j])
+                                                 : spmv_df(a, s, sm, r0, r1, vj, sm->scale[j]);
                     else
-                        om[0] = spmv<true>(a, s, sm, r0, r1, vj, __dmul_rn(sm->scale[j], s.pscale), a.valp, false);
+                        om[0] = a.spmv_lanes > 1 ? spmv_lanes<true>(a, s, sm, r0, r1, vj, xs, a.valp, false)
+                                                 : spmv<true>(a, s, sm, r0, r1, vj, xs, a.valp, false);
                     __syncthreads();
                     block_sum<1>(sm, om, 1, j + 1);              // red[j+1] = omega^2 partial
                     dot(a, s, sm, r0, r1, j + 1);                // red[0..j]

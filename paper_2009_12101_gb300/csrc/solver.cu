@@ -102,6 +102,8 @@ const Ops& ops_for(int fmt)
 
 long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
 
+constexpr long long SPMV_TUNE_MIN_ROWS = 65536;   // create times the SpMV schedules from here on
+
 // Next basis format of the adaptive ladder (options.adapt): e4m3 -> bf16 -> f32 -> f64,
 // f16 -> f32, i16 -> i32 -> f64; -1 at the top.
 int promote_format(int fmt)
@@ -461,6 +463,11 @@ template <class T> int dalloc(T** p, size_t count)
         return e == cudaErrorMemoryAllocation ? CBG_ERR_OOM : CBG_ERR_CUDA;
     }
     return CBG_OK;
+}
+
+int spmv_grid(long long n, int group, int sms, int occ)
+{
+    return std::max(1, (int)std::min<long long>((n * group + THREADS - 1) / THREADS, (long long)sms * occ));
 }
 
 int pick_group(long long n, long long nnz)
@@ -1121,12 +1128,12 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->fmt0 = fmt;
     h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
     h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
-    h->grid_spmv = (int)std::min<long long>((n * h->group + THREADS - 1) / THREADS, (long long)sms * occ_spmv);
+    h->grid_spmv = spmv_grid(n, h->group, sms, occ_spmv);
     h->grid_store = std::max(1, h->grid_store);
-    h->grid_spmv = std::max(1, h->grid_spmv);
     h->grid_tma = sms;
     h->use_tma = o.arith == CBG_ARITH_DF32;
-    h->gridmax = std::max(std::max(h->grid_store, h->grid_spmv), h->grid_tma);
+    // (room for the SpMV partials of every lane count the create-time tuning may pick)
+    h->gridmax = std::max(std::max(h->grid_store, spmv_grid(n, 32, sms, occ_spmv)), h->grid_tma);
     for (int f = fmt; f >= 0; f = o.adapt ? promote_format(f) : -1) {
         if (o.arith == CBG_ARITH_DF32 && !ops_for(f).tma_fits()) TRY(CBG_ERR_UNSUPPORTED);
         set_format(h, f);
@@ -1180,6 +1187,47 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     h->step_ev.resize(L, nullptr);
     for (auto& e : h->step_ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) TRY(CBG_ERR_CUDA);
+    // Automatic SpMV schedule on large matrices: time the per-step SpMV with 1, 2, ..., 32
+    // lanes per row on this matrix (on the zero first basis column; the access pattern
+    // does not depend on the values) and keep the fastest.
+    if (!o.spmv_group && n >= SPMV_TUNE_MIN_ROWS) {
+        double one = 1.0;
+        if (cudaMemcpy(h->d.scales, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) TRY(CBG_ERR_CUDA);
+        float best = 1e30f;
+        int best_g = h->group;
+        for (int g = 1; g <= 32; g *= 2) {
+            SpmvArgs a = spmv_args(h);
+            a.xscale_dev = h->d.scales;
+            a.x = h->V;
+            a.val = h->valp ? h->valp : h->val;
+            a.y = h->w;
+            a.ydf = h->opt.arith == CBG_ARITH_DF32 ? reinterpret_cast<float*>(h->wdf) : nullptr;
+            a.ydf_ld = h->ld;
+            a.valdf = a.ydf ? h->valdf : nullptr;
+            a.nnz = h->nnz;
+            a.xexp = a.valdf ? 0 : h->pexp;
+            a.counter = h->d.counters + 1;
+            const int grid = spmv_grid(n, g, sms, occ_spmv);
+            const Ops& op = ops_for(fmt);
+            op.spmv_code(SPMV_ARNOLDI, g, grid, h->stream, a);                      // warm
+            cudaEventRecord(t0, h->stream);
+            for (int rep = 0; rep < 3; rep++) op.spmv_code(SPMV_ARNOLDI, g, grid, h->stream, a);
+            cudaEventRecord(t1, h->stream);
+            float ms = 0.f;
+            if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                TRY(CBG_ERR_CUDA);
+            }
+            if (ms < best) { best = ms; best_g = g; }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        h->group = best_g;
+        h->grid_spmv = spmv_grid(n, best_g, sms, occ_spmv);
+    }
     if (o.profile) {
         const int pairs = 8 * restart + 64;
         h->prof_ev.resize(2 * pairs, nullptr);
@@ -1270,6 +1318,8 @@ int cbgmres_basis_column(cbg_handle* h, int col, double* out)
     CBG_CUDA(cudaStreamSynchronize(h->stream));
     return CBG_OK;
 }
+
+int cbgmres_spmv_group(const cbg_handle* h) { return h ? h->group : CBG_ERR_ARG; }
 
 int cbgmres_test_stall(cbg_handle* h, int dots, long long wait_cycles)
 {

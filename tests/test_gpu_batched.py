@@ -49,6 +49,32 @@ def test_batched_matches_oracle(fmt, schedule, use_graph):
         _check_against_oracle(mats, bs, x.cpu().numpy(), out, fmt, 1e-8)
 
 
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("fmt", ["f64", "f32", "f16"])
+def test_batched_spmv_lanes_match_oracle(fmt, lanes):
+    """The SpMV schedules the tuner chooses from (2, 4 or 8 lanes per row, the lanes
+    splitting a row's nonzeros) give the oracle's solutions, with clusters and single
+    blocks."""
+    torch, cb = need_gpu()
+    mats, bs = _batch(24, 200, 6000)
+    with cb.BatchedSolver(mats, restart=30, fmt=fmt, precond="jacobi", use_graph=True) as bt:
+        bt.schedule(4, 1500)
+        assert bt.spmv_lanes(lanes) == lanes
+        b = torch.from_numpy(np.concatenate(bs)).cuda()
+        x = torch.zeros(bt.total, dtype=torch.float64, device="cuda")
+        out = bt.solve(b, x, tol=1e-8)
+        assert out["status"] == 0
+        _check_against_oracle(mats, bs, x.cpu().numpy(), out, fmt, 1e-8)
+    # without a preconditioner the per-step SpMV takes A's own values (FP64 path for f64)
+    with cb.BatchedSolver(mats[:6], restart=30, fmt=fmt, precond="none") as bt:
+        bt.spmv_lanes(lanes)
+        b = torch.from_numpy(np.concatenate(bs[:6])).cuda()
+        x = torch.zeros(bt.total, dtype=torch.float64, device="cuda")
+        out = bt.solve(b, x, tol=1e-8)
+        assert out["status"] == 0
+        _check_against_oracle(mats[:6], bs[:6], x.cpu().numpy(), out, fmt, 1e-8, precond=O.PC_NONE)
+
+
 @pytest.mark.parametrize("case", ["one", "tiny", "huge", "wide"])
 def test_batched_without_preconditioner(case):
     """No preconditioner, restart 64: the per-step SpMV takes A's own values, normalised by a
@@ -75,8 +101,12 @@ def test_batched_zero_rhs_and_tuner(tmp_path):
         b = torch.from_numpy(np.concatenate(bs)).cuda()
         x = torch.zeros(bt.total, dtype=torch.float64, device="cuda")
         c1, s1 = bt.tune(b, x, tol=1e-8, cache_path=cache)
+        l1 = bt.spmv_lanes()
+        bt.spmv_lanes(8 if l1 != 8 else 1)
         c2, s2 = bt.tune(b, x, tol=1e-8, cache_path=cache)     # served from the cache
         assert (c1, s1) == (c2, s2) and c1 >= 1
+        assert bt.spmv_lanes() == l1 and l1 in (1, 2, 4, 8)
+        assert '"lanes": ' in open(cache).read()
         x.zero_()
         out = bt.solve(b, x, tol=1e-8)
     assert out["status"] == 0 and out["iters"][3] == 0

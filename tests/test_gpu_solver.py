@@ -460,3 +460,30 @@ def test_stall_needs_the_pipelined_dot():
         with pytest.raises(cb.CbgError) as e:
             s.test_stall(1, 1000)
     assert e.value.status == -6
+
+
+def test_spmv_schedule_tuned_at_create():
+    """On a matrix of at least 65,536 rows the handle times 1, 2, ..., 32 lanes per CSR
+    row at create and keeps the fastest; every schedule gives the oracle's first
+    Hessenberg columns, and the tuned handle solves to the oracle's iterations and x."""
+    torch, cb = need_gpu()
+    A = W.convdiff3d(48)                       # n = 110,592
+    xs = W.exact_solution(A.n, 2)
+    b = W.rhs_from_solution(A, xs)
+    k, tol = 10, 1e-10
+    r1 = O.gmres(A, b, m=100, fmt=O.F32, tol=0.0, maxit=k, want_H1=True)
+    bd = to_dev(torch, b)
+    for g in (1, 4, 32):
+        with cb.Solver.from_csr(A, restart=100, fmt="f32", spmv_group=g) as s:
+            assert s.spmv_group() == g
+            Hg = s.arnoldi(bd, torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+            assert np.all(col_relerr(Hg, r1["H1"], k) <= 1e-10)
+    ro = O.gmres(A, b, m=100, fmt=O.F32, tol=tol, maxit=20000)
+    with cb.Solver.from_csr(A, restart=100, fmt="f32") as s:
+        assert s.spmv_group() in (1, 2, 4, 8, 16, 32)
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(bd, xg, tol=tol, maxit=20000)
+    assert st["status"] == 0
+    x = xg.cpu().numpy()
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
