@@ -124,10 +124,13 @@ typedef struct {
     int32_t reorth;          /* cbg_reorth, default CBG_REORTH_ALWAYS (CGS + 1 pass)   */
     int32_t precond;         /* cbg_precond, default CBG_PC_NONE                       */
     int32_t arith;           /* cbg_arith, default CBG_ARITH_DF32                      */
-    int32_t spmv_group;      /* lanes per CSR row: 0 = automatic, else 1..32 (pow2):   *
-                              * automatic times 1, 2, .., 32 lanes at create on       *
-                              * matrices of >= 65536 rows and keeps the fastest, and  *
-                              * picks by nonzeros per row below that                  */
+    int32_t spmv_group;      /* lanes per CSR row: 0 = automatic, else 1..32 (pow2),   *
+                              * or -1 = the per-step SpMV on a sliced-ELL copy        *
+                              * (DF32 arithmetic; padding <= nnz/4, else              *
+                              * CBG_ERR_UNSUPPORTED).  Automatic times 1, 2, .., 32    *
+                              * lanes and the sliced-ELL copy at create on matrices   *
+                              * of >= 65536 rows and keeps the fastest, and picks by  *
+                              * nonzeros per row below that                           */
     double eta;              /* conditional re-orthogonalisation threshold (1/sqrt 2)  */
     double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
     void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
@@ -286,7 +289,9 @@ int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64
                              int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                              void* stream, int path);
 
-/* Lanes per CSR row of the handle's SpMV (the tuned or given schedule), or CBG_ERR_ARG. */
+/* Lanes per CSR row of the handle's SpMV (the tuned or given schedule); 0 when the
+ * create-time timing chose the sliced-ELL copy of the double-float values (chunks of 32
+ * rows, one coalesced load per warp and entry) for the per-step SpMV; or CBG_ERR_ARG. */
 int cbgmres_spmv_group(const cbg_handle* h);
 
 /* Test of the failure path (no counterpart in the paper).  The next `dots` launches of

@@ -946,6 +946,121 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     }
 }
 
+// ================================================== SpMV on a sliced-ELL copy of the matrix
+// The per-step SpMV (Arnoldi mode, double-float rows) on the matrix re-laid out in chunks
+// of 32 consecutive rows (sliced ELLPACK with slice 32): chunk c holds len[c] = the
+// longest row of the chunk, entry k of the chunk's row `lane` at off[c] + 32 k + lane
+// (shorter rows padded with zero values and an in-range column).  A warp owns a chunk and
+// a lane its row, so every load of the column indices and of the split values is one
+// coalesced 128-byte access (the CSR kernel's thread-per-row loads stride by the row
+// length); only the gather of x stays irregular (it hits L2: x is one basis column).
+// Same arithmetic as k_spmv's double-float rows: TwoProd per nonzero, TwoSum per add.
+struct SellArgs {
+    const int* len;           // [nchunks] entries per row of the chunk
+    const long long* off;     // [nchunks] first entry of the chunk
+    const int* col;           // [entries] column indices
+    const float* val;         // [2 * entries]: FP32 hi plane, then lo plane
+    long long entries;
+    long long nchunks;
+    long long n;
+    const void* x;            // code column (XFMT >= 0) or FP64 vector (XFMT < 0)
+    const double* xscale_dev; // decode scale of the code column (may be null: 1)
+    float* ydf;               // y as double-float planes hi[ydf_ld], lo[ydf_ld]
+    long long ydf_ld;
+    double* part;             // [gridDim.x][2] per-block sum of squares (and 0)
+    unsigned int* counter;
+    DevState* st;             // omega = ||y|| (last block)
+    const int* active;        // skip when *active == 0 (may be null)
+};
+
+template <int XFMT>
+__global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
+{
+    if (a.active && *a.active == 0) return;
+    __shared__ double red_s[THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr bool XEXACT = XFMT == F32 || XFMT == F16 || XFMT == BF16 || XFMT == E4M3 || XFMT == I16;
+    const double xs = a.xscale_dev ? *a.xscale_dev : 1.0;
+    const bool xsplit = xs != 1.0;
+    float xsh = 1.f, xsl = 0.f;
+    if (xsplit) split_f64(xs, xsh, xsl);
+    const float* vh = a.val;
+    const float* vl = a.val + a.entries;
+    float ssS = 0.f, ssC = 0.f;
+    auto dfadd = [](float& S, float& C, float pr, float er) {   // (S, C) += pr + er
+        const float t = __fadd_rn(S, pr), bb = __fsub_rn(t, S);
+        C = __fadd_rn(C, __fadd_rn(__fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(pr, bb)), er));
+        S = t;
+    };
+    for (long long c = (long long)blockIdx.x * (THREADS / 32) + warp; c < a.nchunks;
+         c += (long long)gridDim.x * (THREADS / 32)) {
+        const int len = a.len[c];
+        const long long p0 = a.off[c] + lane;
+        float S = 0.f, C = 0.f;
+        int k = 0;
+        for (; k + 2 <= len; k += 2) {                 // two entries' loads in flight
+            const long long p = p0 + 32ll * k, q = p + 32;
+            const int c0 = a.col[p], c1 = a.col[q];
+            const float h0 = vh[p], l0 = vl[p], h1 = vh[q], l1 = vl[q];
+            float x0h, x0l, x1h, x1l;
+            xval_df<XFMT>(a.x, c0, x0h, x0l);
+            xval_df<XFMT>(a.x, c1, x1h, x1l);
+            float pr = __fmul_rn(h0, x0h), er = __fmaf_rn(h0, x0h, -pr);
+            er = __fmaf_rn(l0, x0h, er);
+            if constexpr (!XEXACT) er = __fmaf_rn(h0, x0l, er);
+            dfadd(S, C, pr, er);
+            pr = __fmul_rn(h1, x1h);
+            er = __fmaf_rn(h1, x1h, -pr);
+            er = __fmaf_rn(l1, x1h, er);
+            if constexpr (!XEXACT) er = __fmaf_rn(h1, x1l, er);
+            dfadd(S, C, pr, er);
+        }
+        if (k < len) {
+            const long long p = p0 + 32ll * k;
+            float xh, xl;
+            xval_df<XFMT>(a.x, a.col[p], xh, xl);
+            const float h0 = vh[p];
+            const float pr = __fmul_rn(h0, xh);
+            float er = __fmaf_rn(h0, xh, -pr);
+            er = __fmaf_rn(vl[p], xh, er);
+            if constexpr (!XEXACT) er = __fmaf_rn(h0, xl, er);
+            dfadd(S, C, pr, er);
+        }
+        const long long row = c * 32 + lane;
+        if (row < a.n) {
+            float hi, lo;
+            two_sum(S, C, hi, lo);                       // renormalise
+            if (xsplit) {                                // integer / power-of-two scales
+                const float p = __fmul_rn(hi, xsh);
+                float e = __fmaf_rn(hi, xsh, -p);
+                e = __fmaf_rn(hi, xsl, e);
+                e = __fmaf_rn(lo, xsh, e);
+                two_sum(p, e, hi, lo);
+            }
+            a.ydf[row] = hi;
+            a.ydf[a.ydf_ld + row] = lo;
+            const float p = __fmul_rn(hi, hi);           // ||y||^2 in double-float
+            float e = __fmaf_rn(hi, hi, -p);
+            e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
+            dfadd(ssS, ssC, p, e);
+        }
+    }
+    double ss = warp_sum(df_to_double(ssS, ssC));
+    if (lane == 0) red_s[warp] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < THREADS / 32; w++) t += red_s[w];
+        a.part[2 * blockIdx.x] = t;
+        a.part[2 * blockIdx.x + 1] = 0.0;
+    }
+    if (last_block(a.counter) && threadIdx.x < 32) {
+        double s2, m2;
+        reduce_norm_parts(a.part, gridDim.x, s2, m2);
+        if (threadIdx.x == 0) a.st->omega = sqrt(s2);
+    }
+}
+
 // ================================================================ codec test kernels
 template <int FMT>
 __global__ void k_encode_vec(const double* v, long long n, unsigned char* codes, EncParams ep)

@@ -18,6 +18,8 @@ template <int FMT> struct Launcher {
     static bool tma_fits();
     static void store(int grid, cudaStream_t s, const StoreArgs& a);
     static void spmv_code(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a);
+    // per-step SpMV on the sliced-ELL copy (Arnoldi mode, double-float rows)
+    static void spmv_sell(int grid, cudaStream_t s, const SellArgs& a);
     static void encode(int grid, cudaStream_t s, const double* v, long long n, unsigned char* codes,
                        EncParams ep);
     static void decode(int grid, cudaStream_t s, const unsigned char* codes, long long n, double scale,
@@ -31,6 +33,7 @@ template <int FMT> struct Launcher {
 
 // SpMV with an FP64 input vector (residual, SPAI second stage, x += P t)
 void spmv_f64(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a);
+void spmv_sell_f64(int grid, cudaStream_t s, const SellArgs& a);
 int spmv_occupancy();
 
 }  // namespace cbg

@@ -79,6 +79,11 @@ void Launcher<FMT>::spmv_code(int mode, int group, int grid, cudaStream_t s, con
     else { CBG_SPMV_GROUPS(FMT, SPMV_PLAIN) }
 }
 
+template <int FMT> void Launcher<FMT>::spmv_sell(int grid, cudaStream_t s, const SellArgs& a)
+{
+    k_spmv_sell<FMT><<<grid, THREADS, 0, s>>>(a);
+}
+
 template <int FMT>
 void Launcher<FMT>::encode(int grid, cudaStream_t s, const double* v, long long n, unsigned char* codes,
                            EncParams ep)

@@ -26,7 +26,7 @@ using namespace cbg;
 
 void cbg_record_cuda_error(cudaError_t e);   // solver.cu
 size_t cbg_tc_multi_workspace(int64_t ld);   // multi_tc.cu
-int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k, const double* W,
+int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k, int ldh, const double* W,
                  int64_t ldw, double* H, void* workspace, cudaStream_t s, int** fault_out);
 
 namespace {
@@ -35,6 +35,7 @@ constexpr int MT = 256;              // threads per block
 constexpr int MNW = MT / 32;
 constexpr int TR = 1024;             // rows per tile
 constexpr int KMAX = 8;              // right-hand sides per launch
+constexpr int KCALL = 64;            // right-hand sides per call (groups of KMAX)
 
 struct MultiArgs {
     const unsigned char* V;
@@ -47,6 +48,7 @@ struct MultiArgs {
     unsigned int* counter;
     double* H;                // [ncols][k] (row-major), device
     int k;                    // vectors actually requested (<= KR)
+    int ldh;                  // row stride of H (>= k)
 };
 
 // W (n x k, column-major, leading dimension ldw) -> hi / lo FP32 planes of KR x ld, zero
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(MT, 1) k_dot_multi(MultiArgs a)
             for (unsigned int b = lane; b < gridDim.x; b += 32)
                 sum += __ldcg(a.part + (long long)b * ncols * KR + col * KR + r);
             sum = warp_sum(sum);
-            if (lane == 0) a.H[i] = sum * a.scales[col];
+            if (lane == 0) a.H[(long long)col * a.ldh + r] = sum * a.scales[col];
         }
     }
 }
@@ -219,33 +221,12 @@ int multi_grid()
     return 2 * std::max(1, sms);
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t cbg_basis_dot_multi_workspace(int64_t ld, int ncols, int k)
+// one group of k <= KMAX vectors: H[c * ldh + r]
+int dot_multi_group(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
+                    const double* W, int64_t ldw, double* H, int ldh, void* workspace, cudaStream_t s, bool tc)
 {
-    if (ld < 1 || ncols < 1 || ncols > MAXCOLS || k < 1 || k > KMAX) return 0;
-    const int KR = kr_for(k);
-    const size_t split = (size_t)2 * KR * ld * sizeof(float);
-    const size_t part = (size_t)multi_grid() * ncols * KR * sizeof(double);
-    const size_t cuda_core = 256 + (split + 255) / 256 * 256 + (part + 255) / 256 * 256;
-    return std::max(cuda_core, cbg_tc_multi_workspace(ld));
-}
-
-int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
-                             const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes, void* stream,
-                             int path)
-{
-    if (cbgmres_format_bytes(fmt) == 0 || n < 1 || ncols < 1 || ncols > MAXCOLS || k < 1 || k > KMAX || !V ||
-        ld < n || ld % TILE_ROWS || !scales || !W || ldw < n || !H || !workspace ||
-        ws_bytes < cbg_basis_dot_multi_workspace(ld, ncols, k) || path < 0 || path > 2)
-        return CBG_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const bool tc_ok = fmt == CBG_F16 && ncols <= 128;
-    if (path == 2 && !tc_ok) return CBG_ERR_UNSUPPORTED;
-    if (path == 2 || (path == 0 && tc_ok)) {
-        int rc = cbg_tc_multi(n, ncols, V, ld, scales, k, W, ldw, H, workspace, s, nullptr);
+    if (tc) {
+        int rc = cbg_tc_multi(n, ncols, V, ld, scales, k, ldh, W, ldw, H, workspace, s, nullptr);
         if (rc) { cbg_record_cuda_error(cudaGetLastError()); return rc; }
         return CBG_OK;
     }
@@ -270,12 +251,49 @@ int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64
     a.counter = counter;
     a.H = H;
     a.k = k;
+    a.ldh = ldh;
     const int grid = multi_grid();
     if (KR == 2) launch_fmt<2>(fmt, grid, s, a);
     else if (KR == 4) launch_fmt<4>(fmt, grid, s, a);
     else launch_fmt<8>(fmt, grid, s, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { cbg_record_cuda_error(e); return CBG_ERR_CUDA; }
+    return CBG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cbg_basis_dot_multi_workspace(int64_t ld, int ncols, int k)
+{
+    if (ld < 1 || ncols < 1 || ncols > MAXCOLS || k < 1 || k > KCALL) return 0;
+    const int KR = kr_for(std::min(k, KMAX));
+    const size_t split = (size_t)2 * KR * ld * sizeof(float);
+    const size_t part = (size_t)multi_grid() * ncols * KR * sizeof(double);
+    const size_t cuda_core = 256 + (split + 255) / 256 * 256 + (part + 255) / 256 * 256;
+    return std::max(cuda_core, cbg_tc_multi_workspace(ld));
+}
+
+int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k,
+                             const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes, void* stream,
+                             int path)
+{
+    if (cbgmres_format_bytes(fmt) == 0 || n < 1 || ncols < 1 || ncols > MAXCOLS || k < 1 || k > KCALL || !V ||
+        ld < n || ld % TILE_ROWS || !scales || !W || ldw < n || !H || !workspace ||
+        ws_bytes < cbg_basis_dot_multi_workspace(ld, ncols, k) || path < 0 || path > 2)
+        return CBG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tc_ok = fmt == CBG_F16 && ncols <= 128;
+    if (path == 2 && !tc_ok) return CBG_ERR_UNSUPPORTED;
+    const bool tc = path == 2 || (path == 0 && tc_ok);
+    // groups of up to KMAX vectors, one after the other on the stream (the workspace is reused)
+    for (int r0 = 0; r0 < k; r0 += KMAX) {
+        const int kg = std::min(KMAX, k - r0);
+        int rc = dot_multi_group(fmt, n, ncols, V, ld, scales, kg, W + (long long)r0 * ldw, ldw, H + r0, k, workspace,
+                                 s, tc);
+        if (rc) return rc;
+    }
     return CBG_OK;
 }
 

@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_dot_multi_tc(TcArgs a)
 // H[c][r] = scales[c] * sum over CTAs (in CTA order) and the four (slice, digit half)
 // sums of (S + C) 2^(Eref - 54 + ps): one warp per entry, so the FP64 work (slow on this
 // GPU) is spread over the device
-__global__ void k_reduce_tc(const float2* part, const int* eref, int nparts, int ncols, int k,
+__global__ void k_reduce_tc(const float2* part, const int* eref, int nparts, int ncols, int k, int ldh,
                             const double* scales, const int* bad, const int* fault, double* H)
 {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
@@ -572,7 +572,8 @@ __global__ void k_reduce_tc(const float2* part, const int* eref, int nparts, int
         sum = __fma_rn(e ? df_to_double(S.y, C.y) : df_to_double(S.x, C.x), sc, sum);
     }
     sum = warp_sum(sum);
-    if (lane == 0) H[i] = (*bad || *fault) ? __longlong_as_double(0x7FF8000000000000ll) : sum * scales[col];
+    if (lane == 0)
+        H[(long long)col * ldh + r] = (*bad || *fault) ? __longlong_as_double(0x7FF8000000000000ll) : sum * scales[col];
 }
 
 int tc_grid()
@@ -594,7 +595,7 @@ size_t cbg_tc_multi_workspace(int64_t ld)
     return 256 + g * 4 * 8 * TC_M * sizeof(float2) + g * NVEC * sizeof(int);
 }
 
-int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k, const double* W,
+int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* scales, int k, int ldh, const double* W,
                  int64_t ldw, double* H, void* workspace, cudaStream_t s, int** fault_out)
 {
     unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -623,6 +624,6 @@ int cbg_tc_multi(int64_t n, int ncols, const void* V, int64_t ld, const double* 
     a.fault = fault;
     a.bad = bad;
     k_dot_multi_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(a);
-    k_reduce_tc<<<(ncols * k * 32 + 255) / 256, 256, 0, s>>>(part, eref, grid, ncols, k, scales, bad, fault, H);
+    k_reduce_tc<<<(ncols * k * 32 + 255) / 256, 256, 0, s>>>(part, eref, grid, ncols, k, ldh, scales, bad, fault, H);
     return cudaGetLastError() == cudaSuccess ? CBG_OK : CBG_ERR_CUDA;
 }

@@ -79,6 +79,7 @@ struct Ops {
     bool (*tma_fits)();
     void (*store)(int, cudaStream_t, const StoreArgs&);
     void (*spmv_code)(int, int, int, cudaStream_t, const SpmvArgs&);
+    void (*spmv_sell)(int, cudaStream_t, const SellArgs&);
     void (*encode)(int, cudaStream_t, const double*, long long, unsigned char*, EncParams);
     void (*decode)(int, cudaStream_t, const unsigned char*, long long, double, double*);
     int (*occ_dot)();
@@ -88,7 +89,7 @@ struct Ops {
 template <int F> Ops make_ops()
 {
     return Ops{&Launcher<F>::dot, &Launcher<F>::axpy, &Launcher<F>::dot_tma,
-               &Launcher<F>::tma_fits, &Launcher<F>::store, &Launcher<F>::spmv_code,
+               &Launcher<F>::tma_fits, &Launcher<F>::store, &Launcher<F>::spmv_code, &Launcher<F>::spmv_sell,
                &Launcher<F>::encode, &Launcher<F>::decode, &Launcher<F>::occupancy_dot,
                &Launcher<F>::occupancy_axpy};
 }
@@ -162,6 +163,46 @@ __global__ void k_split_df_pow2(const double* v, long long n, int e, float* out)
         split_f64(__dmul_rn(v[i], sc), h, l);
         out[i] = h;
         out[n + i] = l;
+    }
+}
+
+// Sliced-ELL copy: entries per row of every chunk of 32 rows (a warp per chunk)
+__global__ void k_sell_len(const int* rowptr, long long n, long long nchunks, int* len)
+{
+    const int lane = threadIdx.x & 31;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+         c += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long row = c * 32 + lane;
+        int l = row < n ? rowptr[row + 1] - rowptr[row] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(0xffffffffu, l, o));
+        if (lane == 0) len[c] = l;
+    }
+}
+
+// ... and the entries: the split values (CSR-order planes valdf[2 * nnz]) and columns in
+// chunk order, padding with zero values and the row's own index (rows past n: column 0)
+__global__ void k_sell_fill(const int* rowptr, const int* col, const float* valdf, long long nnz, long long n,
+                            long long nchunks, const int* len, const long long* off, long long entries, int* scol,
+                            float* sval)
+{
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < nchunks * 32;
+         row += (long long)gridDim.x * blockDim.x) {
+        const long long c = row >> 5;
+        const int lane = (int)(row & 31), L = len[c];
+        const int p0 = row < n ? rowptr[row] : 0, cnt = row < n ? rowptr[row + 1] - p0 : 0;
+        for (int k = 0; k < L; k++) {
+            const long long q = off[c] + 32ll * k + lane;
+            if (k < cnt) {
+                scol[q] = col[p0 + k];
+                sval[q] = valdf[p0 + k];
+                sval[entries + q] = valdf[nnz + p0 + k];
+            } else {
+                scol[q] = row < n ? (int)row : 0;
+                sval[q] = 0.f;
+                sval[entries + q] = 0.f;
+            }
+        }
     }
 }
 
@@ -408,6 +449,15 @@ struct cbg_handle {
     int grid_tma = 0;         // bulk-copy pipelined basis kernels: one block per SM
     int fmt0 = 0;             // the handle's basis format (options.adapt may move up from it)
     bool use_tma = false;
+    // sliced-ELL copy of the per-step operator (chunks of 32 rows), used when the
+    // create-time timing finds it faster than the CSR SpMV
+    int* sell_len = nullptr;
+    long long* sell_off = nullptr;
+    int* sell_col = nullptr;
+    float* sell_val = nullptr;
+    long long sell_entries = 0, sell_chunks = 0;
+    bool use_sell = false;
+    int grid_sell = 0;
     int test_stall = 0;            // cbgmres_test_stall: pipelined dots still to be stalled
     long long test_wait = 0;       //   and their wait limit in clock cycles
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -430,6 +480,7 @@ void free_handle(cbg_handle* h)
     if (h->own_ppat) { cudaFree(h->prow); cudaFree(h->pcol); }
     cudaFree(h->pvals); cudaFree(h->V); cudaFree(h->w); cudaFree(h->wdf); cudaFree(h->w1); cudaFree(h->w2); cudaFree(h->r);
     cudaFree(h->tmp); cudaFree(h->z); cudaFree(h->bdev); cudaFree(h->xdev); cudaFree(h->scratch);
+    cudaFree(h->sell_len); cudaFree(h->sell_off); cudaFree(h->sell_col); cudaFree(h->sell_val);
     cudaFree(h->state_block);
     if (h->d.hist) {   // stream-ordered allocation (see run_solve); the frees above synchronised
         cudaFreeAsync(h->d.hist, 0);
@@ -538,6 +589,27 @@ void set_format(cbg_handle* h, int fmt)
     h->grid_axpy = std::max(1, (int)std::min<long long>(axpy_blocks, (long long)sms * std::max(1, op.occ_axpy())));
 }
 
+SellArgs sell_args(cbg_handle* h, const void* x, const double* xscale_dev, float* ydf, const int* active)
+{
+    SellArgs a{};
+    a.len = h->sell_len;
+    a.off = h->sell_off;
+    a.col = h->sell_col;
+    a.val = h->sell_val;
+    a.entries = h->sell_entries;
+    a.nchunks = h->sell_chunks;
+    a.n = h->n;
+    a.x = x;
+    a.xscale_dev = xscale_dev;
+    a.ydf = ydf;
+    a.ydf_ld = h->ld;
+    a.part = h->d.part_spmv;
+    a.counter = h->d.counters + 1;
+    a.st = h->d.st;
+    a.active = active;
+    return a;
+}
+
 SpmvArgs spmv_args(cbg_handle* h)
 {
     SpmvArgs a{};
@@ -632,7 +704,12 @@ void enqueue_step(cbg_handle* h, int j)
             b2.valdf = wdf ? h->valdf : nullptr;
             b2.nnz = h->nnz;
             b2.counter = h->d.counters + 1;
-            launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
+            if (h->use_sell && wdf) {
+                SellArgs sa2 = sell_args(h, h->z, nullptr, wdf, active);
+                launch(h, 2, spmv_bytes(h), [&] { spmv_sell_f64(h->grid_sell, s, sa2); });                // w = A z
+            } else {
+                launch(h, 2, spmv_bytes(h), [&] { spmv_f64(SPMV_ARNOLDI, h->group, h->grid_spmv, s, b2); });   // w = A z
+            }
         } else {
             a.val = h->valp ? h->valp : h->val;
             a.y = h->w;
@@ -642,7 +719,12 @@ void enqueue_step(cbg_handle* h, int j)
             a.nnz = h->nnz;
             a.xexp = a.valdf ? 0 : h->pexp;          // (the planes hold the scaled values)
             a.counter = h->d.counters + 1;
-            launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
+            if (h->use_sell && wdf) {
+                SellArgs sa1 = sell_args(h, Vj, h->d.scales + j, wdf, active);
+                launch(h, 2, spmv_bytes(h), [&] { op.spmv_sell(h->grid_sell, s, sa1); });
+            } else {
+                launch(h, 2, spmv_bytes(h), [&] { op.spmv_code(SPMV_ARNOLDI, h->group, h->grid_spmv, s, a); });
+            }
         }
     }
     const int ncols = j + 1;
@@ -1010,7 +1092,8 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     if (o.ortho != CBG_ORTHO_CGS && o.ortho != CBG_ORTHO_MGS) return CBG_ERR_ARG;
     if (o.reorth == CBG_REORTH_CONDITIONAL && o.ortho == CBG_ORTHO_MGS) return CBG_ERR_UNSUPPORTED;
     if (o.reorth == CBG_REORTH_CONDITIONAL && !(o.eta > 0.0 && o.eta <= 1.0)) return CBG_ERR_ARG;
-    if (o.spmv_group != 0 && (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
+    if (o.spmv_group != 0 && o.spmv_group != -1 &&
+        (o.spmv_group < 1 || o.spmv_group > 32 || (o.spmv_group & (o.spmv_group - 1))))
         return CBG_ERR_ARG;
 
     // validate the CSR on the host
@@ -1127,7 +1210,7 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     const int occ_spmv = std::max(1, spmv_occupancy());
     h->fmt0 = fmt;
     h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
-    h->group = o.spmv_group ? o.spmv_group : pick_group(n, nnz);
+    h->group = o.spmv_group > 0 ? o.spmv_group : pick_group(n, nnz);
     h->grid_spmv = spmv_grid(n, h->group, sms, occ_spmv);
     h->grid_store = std::max(1, h->grid_store);
     h->grid_tma = sms;
@@ -1189,8 +1272,39 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) TRY(CBG_ERR_CUDA);
     // Automatic SpMV schedule on large matrices: time the per-step SpMV with 1, 2, ..., 32
     // lanes per row on this matrix (on the zero first basis column; the access pattern
-    // does not depend on the values) and keep the fastest.
-    if (!o.spmv_group && n >= SPMV_TUNE_MIN_ROWS) {
+    // does not depend on the values), and on a sliced-ELL copy of the double-float values
+    // when the padding stays below a quarter of the nonzeros, and keep the fastest.
+    const bool tune_spmv = !o.spmv_group && n >= SPMV_TUNE_MIN_ROWS;
+    if ((tune_spmv || o.spmv_group == -1) && h->valdf && o.arith == CBG_ARITH_DF32) {
+        const long long nch = (n + 31) / 32;
+        TRY(dalloc(&h->sell_len, nch));
+        k_sell_len<<<(int)std::min<long long>((nch * 32 + 255) / 256, 4096), 256>>>(h->rowptr, n, nch, h->sell_len);
+        std::vector<int> lens(nch);
+        std::vector<long long> offs(nch);
+        if (cudaMemcpy(lens.data(), h->sell_len, nch * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            TRY(CBG_ERR_CUDA);
+        long long total = 0;
+        for (long long c = 0; c < nch; c++) { offs[c] = total; total += 32ll * lens[c]; }
+        if (total <= nnz + nnz / 4 && total < (1ll << 31)) {
+            h->sell_entries = total;
+            h->sell_chunks = nch;
+            TRY(dalloc(&h->sell_off, nch));
+            TRY(dalloc(&h->sell_col, total));
+            TRY(dalloc(&h->sell_val, 2 * total));
+            if (cudaMemcpy(h->sell_off, offs.data(), nch * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess)
+                TRY(CBG_ERR_CUDA);
+            k_sell_fill<<<(int)std::min<long long>((nch * 32 + 255) / 256, 4096), 256>>>(
+                h->rowptr, h->col, h->valdf, nnz, n, nch, h->sell_len, h->sell_off, total, h->sell_col, h->sell_val);
+            if (cudaGetLastError() != cudaSuccess) TRY(CBG_ERR_CUDA);
+            h->grid_sell = (int)std::max<long long>(1, std::min<long long>((nch + THREADS / 32 - 1) / (THREADS / 32),
+                                                                          (long long)sms * occ_spmv));
+        }
+    }
+    if (o.spmv_group == -1) {                      // the sliced-ELL copy, as asked
+        if (h->sell_entries == 0) TRY(CBG_ERR_UNSUPPORTED);
+        h->use_sell = true;
+    }
+    if (tune_spmv) {
         double one = 1.0;
         if (cudaMemcpy(h->d.scales, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) TRY(CBG_ERR_CUDA);
         cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -1222,6 +1336,18 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
                 TRY(CBG_ERR_CUDA);
             }
             if (ms < best) { best = ms; best_g = g; }
+        }
+        if (h->sell_entries > 0 && h->opt.arith == CBG_ARITH_DF32) {
+            SellArgs sa = sell_args(h, h->V, h->d.scales, reinterpret_cast<float*>(h->wdf), nullptr);
+            const Ops& op = ops_for(fmt);
+            op.spmv_sell(h->grid_sell, h->stream, sa);                                  // warm
+            cudaEventRecord(t0, h->stream);
+            for (int rep = 0; rep < 3; rep++) op.spmv_sell(h->grid_sell, h->stream, sa);
+            cudaEventRecord(t1, h->stream);
+            float ms = 0.f;
+            if (cudaEventSynchronize(t1) == cudaSuccess && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess &&
+                ms < best)
+                h->use_sell = true;
         }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
@@ -1319,7 +1445,7 @@ int cbgmres_basis_column(cbg_handle* h, int col, double* out)
     return CBG_OK;
 }
 
-int cbgmres_spmv_group(const cbg_handle* h) { return h ? h->group : CBG_ERR_ARG; }
+int cbgmres_spmv_group(const cbg_handle* h) { return h ? (h->use_sell ? 0 : h->group) : CBG_ERR_ARG; }
 
 int cbgmres_test_stall(cbg_handle* h, int dots, long long wait_cycles)
 {

@@ -10,6 +10,7 @@ void spmv_f64(int mode, int group, int grid, cudaStream_t s, const SpmvArgs& a)
     else if (mode == SPMV_ACCUM) { CBG_SPMV_GROUPS(-1, SPMV_ACCUM) }
     else { CBG_SPMV_GROUPS(-1, SPMV_PLAIN) }
 }
+void spmv_sell_f64(int grid, cudaStream_t s, const SellArgs& a) { k_spmv_sell<-1><<<grid, THREADS, 0, s>>>(a); }
 int spmv_occupancy()
 {
     int b = 0;

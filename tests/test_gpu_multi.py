@@ -1,5 +1,5 @@
-"""Multi-RHS basis product H = V^T W (k <= 8 vectors sharing one compressed basis)
-against the oracle's dot products, through the C ABI."""
+"""Multi-RHS basis product H = V^T W (k <= 64 vectors sharing one compressed basis, in
+groups of 8) against the oracle's dot products, through the C ABI."""
 import numpy as np
 import pytest
 
@@ -26,7 +26,8 @@ def _basis(fmt, n, ncols, ld, seed):
 
 
 @pytest.mark.parametrize("fmt", FORMATS)
-@pytest.mark.parametrize("n,ncols,k", [(5000, 1, 1), (12289, 13, 3), (40000, 40, 8), (70001, 9, 5), (9000, 101, 4)])
+@pytest.mark.parametrize("n,ncols,k", [(5000, 1, 1), (12289, 13, 3), (40000, 40, 8), (70001, 9, 5), (9000, 101, 4),
+                                        (9000, 37, 16), (4096, 12, 21)])
 def test_basis_dot_multi_matches_oracle(fmt, n, ncols, k):
     torch, cb = need_gpu()
     ld = (n + 4095) // 4096 * 4096
@@ -45,13 +46,14 @@ def test_basis_dot_multi_matches_oracle(fmt, n, ncols, k):
 def test_basis_dot_multi_rejects_bad_arguments():
     torch, cb = need_gpu()
     V = torch.zeros((3, 4096 * 4), dtype=torch.uint8, device="cuda")
-    W = torch.zeros((9, 4096), dtype=torch.float64, device="cuda")
+    W = torch.zeros((65, 4096), dtype=torch.float64, device="cuda")
     with pytest.raises(cb.CbgError):
-        cb.basis_dot_multi("f32", 4096, V, 4096, np.ones(3), W)     # k = 9 > 8
+        cb.basis_dot_multi("f32", 4096, V, 4096, np.ones(3), W)     # k = 65 > 64
 
 
 @pytest.mark.parametrize("n,ncols,k", [(5000, 1, 1), (12289, 13, 3), (40000, 40, 8), (70001, 9, 5),
-                                        (9000, 101, 4), (20480, 128, 8), (2049, 7, 2)])
+                                        (9000, 101, 4), (20480, 128, 8), (2049, 7, 2), (9000, 64, 16),
+                                        (12289, 100, 20)])
 def test_basis_dot_multi_tensor_cores(n, ncols, k):
     """The tcgen05 path (f16 basis): exact digit products on the tensor cores, compared with
     the oracle and with the double-float CUDA-core path."""

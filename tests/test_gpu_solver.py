@@ -480,10 +480,37 @@ def test_spmv_schedule_tuned_at_create():
             assert np.all(col_relerr(Hg, r1["H1"], k) <= 1e-10)
     ro = O.gmres(A, b, m=100, fmt=O.F32, tol=tol, maxit=20000)
     with cb.Solver.from_csr(A, restart=100, fmt="f32") as s:
-        assert s.spmv_group() in (1, 2, 4, 8, 16, 32)
+        assert s.spmv_group() in (0, 1, 2, 4, 8, 16, 32)    # 0: the sliced-ELL copy
         xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
         st = s.solve(bd, xg, tol=tol, maxit=20000)
     assert st["status"] == 0
     x = xg.cpu().numpy()
+    assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+@pytest.mark.parametrize("fmt", ["f64", "f32", "f16", "e4m3", "i32"])
+@pytest.mark.parametrize("prob", ["convdiff20", "random27_small"])
+def test_sliced_ell_spmv_parity(prob, fmt):
+    """The per-step SpMV on the sliced-ELL copy (spmv_group = -1: chunks of 32 rows,
+    padded with zeros; the random matrix's rows all have 27 entries, the stencil's fewer
+    at the boundary): the first 10 Hessenberg columns and the full solve against the
+    oracle."""
+    torch, cb = need_gpu()
+    A, xs, b = _problem(prob)
+    k, m, tol = 10, 100, 1e-10
+    r1 = O.gmres(A, b, m=20, fmt=O.FORMATS[fmt], tol=0.0, maxit=k, want_H1=True)
+    ro = O.gmres(A, b, m=m, fmt=O.FORMATS[fmt], tol=tol, maxit=20000)
+    bd = to_dev(torch, b)
+    with cb.Solver.from_csr(A, restart=20, fmt=fmt, spmv_group=-1) as s:
+        assert s.spmv_group() == 0
+        Hg = s.arnoldi(bd, torch.zeros(A.n, dtype=torch.float64, device="cuda"), k)
+        assert np.all(col_relerr(Hg, r1["H1"], k) <= 1e-10)
+    with cb.Solver.from_csr(A, restart=m, fmt=fmt, spmv_group=-1) as s:
+        xg = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st = s.solve(bd, xg, tol=tol, maxit=20000)
+    assert st["status"] == 0
+    x = xg.cpu().numpy()
+    assert np.linalg.norm(b - O.spmv(A, x)) <= tol * np.linalg.norm(b) * (1 + 1e-9)
     assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
