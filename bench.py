@@ -166,6 +166,14 @@ def measured_tensor_peak():
         return "bf16", "fallback 1700 TFLOP/s sustained", 1700.0
 
 
+def shard_units(nunits: int, world: int, rank: int) -> range:
+    """Contiguous share of rank `rank` out of `world` of nunits independent units (the
+    systems of a batch): sizes differ by at most one, the shares cover every unit once."""
+    base, extra = divmod(nunits, world)
+    lo = rank * base + min(rank, extra)
+    return range(lo, lo + base + (1 if rank < extra else 0))
+
+
 def max_over_ranks(vals: dict, device) -> dict:
     """Element-wise maximum of per-rank timings over all ranks of the process group (the
     slowest replica decides a whole-job time).  Keys must be the same on every rank."""
@@ -350,7 +358,20 @@ def run_batch(args):
     import workloads as W
     cb.ensure_built()
     mats = W.stencil_batch(nsys=args.batch_nsys)
-    xs = [W.exact_solution(A.n, 4, salt=i) for i, A in enumerate(mats)]
+    # under torchrun every rank solves its contiguous share of the systems (no collective
+    # on the data path; the batch time is the slowest rank's)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+        mine = shard_units(len(mats), world, rank)
+        sel = list(mine)
+        mats = [mats[i] for i in sel]
+    else:
+        sel = list(range(len(mats)))
+    xs = [W.exact_solution(A.n, 4, salt=i) for i, A in zip(sel, mats)]
     bs_list = [W.rhs_from_solution(A, x) for A, x in zip(mats, xs)]
     b = np.concatenate(bs_list)
     fmts = ["f64", "f32", "f16"]
@@ -389,13 +410,15 @@ def run_batch(args):
             launches += outs[f]["kernel_launches"]
     clk = clocks.stop()
     t = {f: sum(v) / len(v) for f, v in times.items()}
+    if world > 1:
+        t = max_over_ranks(t, "cuda")
     peak, peak_kind = measured_peaks()
     o = outs["f32"]
     mb = batch_model_bytes(mats, o["iters"], o["restarts"], m, 4)
     achieved = mb / (t["f32"] * 1e-3) / 1e9
     # the same systems one by one through the single-system solver (f32, Jacobi)
     seq_ms = None
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:
         tot = 0.0
         for A, bb in zip(mats, bs_list):
             with cb.Solver.from_csr(A, restart=m, fmt="f32", precond="jacobi") as s1:
@@ -419,10 +442,12 @@ def run_batch(args):
             xh.copy_(xdev); torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         te[f] = sum(ts) / len(ts)
+    if world > 1:
+        te = max_over_ranks(te, "cuda")
     # CPU baseline: the oracle's full solves (f32 basis, Jacobi) of every 32nd system on all
     # host threads and on one, extrapolated to the batch by rows x GPU iterations
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:
         hc = host_cpu()
         pick = list(range(0, len(mats), 32))
         work = lambda idx: sum(mats[i].n * max(1, int(o["iters"][i])) for i in idx)
@@ -438,9 +463,9 @@ def run_batch(args):
                        f"{len(mats)} systems (every 32nd), extrapolated to the batch by rows x GPU iterations",
                        hc, True)
     line = {
-        "metric": METRIC, "value": round(t["f64"] / t["f32"], 4), "unit": "x", "n_gpus": 1,
+        "metric": METRIC, "value": round(t["f64"] / t["f32"], 4), "unit": "x", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(t.values()), 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD.replace("batch512", f"batch{len(mats)}"), "nsys": len(mats),
                    "total_rows": int(b.size), "restart": m,
                    "tol": tol, "formats": fmts, "schedule_cluster_split_lanes": {f: list(v) for f, v in sched.items()},
@@ -463,9 +488,13 @@ def run_batch(args):
                 "d2h_bytes_per_step": 2 * 8 * int(b.size), "seconds": {k: round(v, 4) for k, v in te.items()}},
         "gpu_launches": launches, "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     for s_ in solvers.values():
         s_.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
