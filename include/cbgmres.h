@@ -129,8 +129,10 @@ typedef struct {
                               * (DF32 arithmetic; padding <= nnz/4, else              *
                               * CBG_ERR_UNSUPPORTED).  Automatic times 1, 2, .., 32    *
                               * lanes and the sliced-ELL copy at create on matrices   *
-                              * of >= 65536 rows and keeps the fastest, and picks by  *
-                              * nonzeros per row below that                           */
+                              * of >= 65536 rows (shortest of 5 launches each) and    *
+                              * keeps the fastest, the copy only when 3 % faster than *
+                              * every CSR schedule (else it is freed); below 65536    *
+                              * rows it picks by nonzeros per row                     */
     double eta;              /* conditional re-orthogonalisation threshold (1/sqrt 2)  */
     double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
     void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
@@ -288,6 +290,16 @@ int cbg_basis_dot_multi(int fmt, int64_t n, int ncols, const void* V, int64_t ld
 int cbg_basis_dot_multi_path(int fmt, int64_t n, int ncols, const void* V, int64_t ld, const double* scales,
                              int k, const double* W, int64_t ldw, double* H, void* workspace, size_t ws_bytes,
                              void* stream, int path);
+
+/* Debug build only (libcbgmres_debug.so, compiled with -DCBG_DEBUG): every device
+ * allocation of the single-system solver carries a 4 KiB guard tail of 0xA5 bytes, and
+ * cbgmres_solve checks every live guard after the solve (CBG_ERR_CUDA, with
+ * cbgmres_last_error naming the overrun, if one was overwritten); the SpMV kernels check
+ * every column index against n and skip one that is out of range, and the next solver
+ * synchronisation returns CBG_ERR_ARG.  This entry point checks the guards now; poke != 0
+ * first overwrites one guard byte of h's basis (a test of the check).  The release build
+ * returns CBG_ERR_UNSUPPORTED. */
+int cbgmres_debug_guard_check(cbg_handle* h, int poke);
 
 /* Lanes per CSR row of the handle's SpMV (the tuned or given schedule); 0 when the
  * create-time timing chose the sliced-ELL copy of the double-float values (chunks of 32

@@ -17,8 +17,14 @@ import threading
 
 import numpy as np
 
-from .build import LIB as _LIB_PATH
+from .build import LIB as _LIB_RELEASE
+from .build import LIB_DEBUG as _LIB_DEBUG
 from .build import build as _build
+
+# CBG_DEBUG=1 in the environment selects the debug library (guard tails on the solver's
+# device allocations checked after every solve, column-index checks in the SpMV)
+DEBUG = os.environ.get("CBG_DEBUG", "0") == "1"
+_LIB_PATH = _LIB_DEBUG if DEBUG else _LIB_RELEASE
 
 FORMATS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "e4m3": 4, "i32": 5, "i16": 6}
 FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
@@ -74,8 +80,13 @@ _lock = threading.Lock()
 
 
 def ensure_built() -> str:
-    """Compile libcbgmres.so for sm_103a if it is missing or older than its sources."""
-    return _build()
+    """Compile libcbgmres.so (libcbgmres_debug.so when CBG_DEBUG=1) for sm_103a if it is
+    missing or older than its sources."""
+    return _build(debug=DEBUG)
+
+
+def lib_path() -> str:
+    return _LIB_PATH
 
 
 def lib():
@@ -105,6 +116,7 @@ def lib():
             L.cbgmres_profile.argtypes = [vp, C.POINTER(Profile), i32]
             L.cbgmres_test_stall.argtypes = [vp, i32, C.c_int64]
             L.cbgmres_spmv_group.argtypes = [vp]
+            L.cbgmres_debug_guard_check.argtypes = [vp, i32]
             L.cbgmres_destroy.argtypes = [vp]
             L.cbgmres_destroy.restype = None
             L.cbg_encode.argtypes = [i32, i64, vp, d, vp, C.POINTER(d), vp]
@@ -309,6 +321,12 @@ class Solver:
         _check(lib().cbgmres_profile(self._h, C.byref(p), int(reset)), "cbgmres_profile")
         return {c: {"ms": p.ms[i], "bytes": p.bytes[i], "launches": p.launches[i]}
                 for i, c in enumerate(PROFILE_CLASSES)}
+
+    def debug_guard_check(self, poke: bool = False) -> int:
+        """Debug library: status of the guard tails of every live allocation (poke: first
+        overwrite one guard byte of this handle's basis, as a test); CBG_ERR_UNSUPPORTED
+        (-6) from the release library."""
+        return int(lib().cbgmres_debug_guard_check(self._h, int(bool(poke))))
 
     def spmv_group(self) -> int:
         """Lanes per CSR row of this handle's SpMV (tuned at create on large matrices)."""

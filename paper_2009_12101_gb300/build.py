@@ -18,6 +18,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcbgmres.so")
+# debug variant (-DCBG_DEBUG): guard tails on the solver's device allocations, checked
+# after every solve, and column-index checks in the SpMV kernels
+LIB_DEBUG = os.path.join(OUT_DIR, "libcbgmres_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["solver.cu", "spmv_f64.cu", "noalloc.cu", "batched.cu", "learned.cu", "mlp_tc.cu", "multi.cu",
            "multi_tc.cu"] + [f"basis_{f}.cu" for f in
@@ -38,15 +41,16 @@ def _newest_source_mtime() -> float:
     return max(t, os.path.getmtime(os.path.join(ROOT, "include", "cbgmres.h")))
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_source_mtime():
-        return LIB
+    lib = LIB_DEBUG if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_source_mtime():
+        return lib
     nvcc = _nvcc()
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    obj_dir = os.path.join(OUT_DIR, "obj_debug" if debug else "obj")
     os.makedirs(obj_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                    "-I", os.path.join(ROOT, "include")]
+                    "-I", os.path.join(ROOT, "include")] + (["-DCBG_DEBUG"] if debug else [])
     if verbose:
         flags += ["-Xptxas", "-v"]
 
@@ -64,14 +68,14 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     if verbose:
         for (_, err), src in zip(results, SOURCES):
             sys.stderr.write(f"== {src}\n{err}")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -9,6 +9,7 @@
 //   vectors FP64 arrays of ld elements, zero padded.
 #pragma once
 #include "cbg_device.cuh"
+#include "cbg_tma.cuh"
 
 namespace cbg {
 
@@ -65,6 +66,24 @@ struct DevArrays {
 };
 
 // ============================================================================ helpers
+// Debug build (-DCBG_DEBUG): a column index outside [0, n) is recorded as FAULT_BOUNDS
+// in the solver state and its entry skipped, instead of being read; release builds
+// compile the check away (the CSR is validated on the host at create).
+__device__ __forceinline__ bool col_ok(int c, long long n, DevState* st)
+{
+#ifdef CBG_DEBUG
+    if ((unsigned long long)(long long)c >= (unsigned long long)n) {
+        if (st) atomicExch(&st->fault, FAULT_BOUNDS);
+        return false;
+    }
+#else
+    (void)c;
+    (void)n;
+    (void)st;
+#endif
+    return true;
+}
+
 __device__ __forceinline__ bool last_block(unsigned int* counter)
 {
     __shared__ bool is_last;
@@ -869,8 +888,10 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
             float S = 0.f, C = 0.f;
             for (int p = p0 + lane_g; p < p1; p += GROUP) {
                 const float vh = a.valdf[p], vl = a.valdf[a.nnz + p];
+                const int cp = a.col[p];
+                if (!col_ok(cp, a.n, a.st)) continue;
                 float xh, xl;
-                xval_df<XFMT>(a.x, a.col[p], xh, xl);
+                xval_df<XFMT>(a.x, cp, xh, xl);
                 const float pr = __fmul_rn(vh, xh);
                 float er = __fmaf_rn(vh, xh, -pr);           // exact product error
                 er = __fmaf_rn(vl, xh, er);
@@ -905,7 +926,10 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
             }
             continue;
         } else {
-            for (int p = p0 + lane_g; p < p1; p += GROUP) s = __fma_rn(a.val[p], xval(a.col[p]), s);
+            for (int p = p0 + lane_g; p < p1; p += GROUP) {
+                const int cp = a.col[p];
+                if (col_ok(cp, a.n, a.st)) s = __fma_rn(a.val[p], xval(cp), s);
+            }
             if constexpr (GROUP > 1) {
 #pragma unroll
                 for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
@@ -1000,8 +1024,10 @@ __global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
         int k = 0;
         for (; k + 2 <= len; k += 2) {                 // two entries' loads in flight
             const long long p = p0 + 32ll * k, q = p + 32;
-            const int c0 = a.col[p], c1 = a.col[q];
-            const float h0 = vh[p], l0 = vl[p], h1 = vh[q], l1 = vl[q];
+            int c0 = a.col[p], c1 = a.col[q];
+            float h0 = vh[p], l0 = vl[p], h1 = vh[q], l1 = vl[q];
+            if (!col_ok(c0, a.n, a.st)) { c0 = 0; h0 = l0 = 0.f; }
+            if (!col_ok(c1, a.n, a.st)) { c1 = 0; h1 = l1 = 0.f; }
             float x0h, x0l, x1h, x1l;
             xval_df<XFMT>(a.x, c0, x0h, x0l);
             xval_df<XFMT>(a.x, c1, x1h, x1l);
@@ -1017,12 +1043,14 @@ __global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
         }
         if (k < len) {
             const long long p = p0 + 32ll * k;
+            int c0 = a.col[p];
+            float h0 = vh[p], l0 = vl[p];
+            if (!col_ok(c0, a.n, a.st)) { c0 = 0; h0 = l0 = 0.f; }
             float xh, xl;
-            xval_df<XFMT>(a.x, a.col[p], xh, xl);
-            const float h0 = vh[p];
+            xval_df<XFMT>(a.x, c0, xh, xl);
             const float pr = __fmul_rn(h0, xh);
             float er = __fmaf_rn(h0, xh, -pr);
-            er = __fmaf_rn(vl[p], xh, er);
+            er = __fmaf_rn(l0, xh, er);
             if constexpr (!XEXACT) er = __fmaf_rn(h0, xl, er);
             dfadd(S, C, pr, er);
         }

@@ -8,6 +8,7 @@ namespace cbg {
 
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
 constexpr int FAULT_TIMEOUT = 1;                        // DevState::fault code
+constexpr int FAULT_BOUNDS = 2;                         // debug build: an index out of range was skipped
 
 __device__ __forceinline__ unsigned smem_addr(const void* p)
 {

@@ -97,3 +97,14 @@ def test_ortho_option_is_checked_before_the_device(libcb):
     for bad_eta in (0.0, -0.5, 1.5, float("nan")):
         o.eta = bad_eta
         assert libcb.cbgmres_create(C.byref(csr), 10, 0, C.byref(o), C.byref(h)) == -1
+
+
+def test_debug_library_builds_and_exports_every_symbol():
+    """The debug variant (-DCBG_DEBUG: guard tails, SpMV index checks) compiles for sm_103a
+    and exports the same entry points."""
+    from paper_2009_12101_gb300 import build as cbuild
+    path = cbuild.build(debug=True)
+    assert path.endswith("libcbgmres_debug.so")
+    L = C.CDLL(path)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing

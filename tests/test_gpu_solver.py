@@ -514,3 +514,35 @@ def test_sliced_ell_spmv_parity(prob, fmt):
     assert np.linalg.norm(b - O.spmv(A, x)) <= tol * np.linalg.norm(b) * (1 + 1e-9)
     assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_debug_build_guards_and_parity():
+    """The debug library (CBG_DEBUG=1, in a subprocess): a solve matches the oracle and
+    leaves every guard tail intact; overwriting one guard byte of the basis is reported."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch
+import oracle as O, workloads as W, paper_2009_12101_gb300 as cb
+cb.ensure_built(); assert cb.lib_path().endswith("libcbgmres_debug.so"), cb.lib_path()
+A = W.convdiff3d(20); xs = W.exact_solution(A.n, 2); b = W.rhs_from_solution(A, xs)
+ro = O.gmres(A, b, m=100, fmt=O.F32, tol=1e-10, maxit=20000)
+with cb.Solver.from_csr(A, restart=100, fmt="f32") as s:
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    st = s.solve(torch.from_numpy(b).cuda(), x, tol=1e-10, maxit=20000)
+    assert st["status"] == 0 and abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"])
+    assert np.linalg.norm(x.cpu().numpy() - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    assert s.debug_guard_check() == 0
+    assert s.debug_guard_check(poke=True) == -4
+    assert b"past the end" in cb.lib().cbgmres_last_error()
+print("debug-ok")
+'''
+    env = dict(os.environ, CBG_DEBUG="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and "debug-ok" in r.stdout, r.stdout + r.stderr
+    torch, cb = need_gpu()
+    with cb.Solver.from_csr(W.poisson2d(8), restart=5, fmt="f32") as s:
+        assert s.debug_guard_check() == -6            # the release library has no guards
