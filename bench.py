@@ -65,6 +65,9 @@ def parse():
                    help="systems of the batch workload (512 is the benchmark; fewer for profiling)")
     p.add_argument("--schedule", type=int, nargs=2, metavar=("CLUSTER", "SPLIT_ROWS"),
                    help="batch workload: this schedule instead of autotuning (for profiling)")
+    p.add_argument("--spmv-group", type=int, default=0,
+                   help="headline workload: SpMV schedule (0: timed at create; k > 0: k lanes per CSR row; "
+                        "-1: the sliced-ELL copy) -- for profiling, where timing under a profiler misleads")
     p.add_argument("--workload", choices=["convdiff128", "batch512", "random27", "learned96", "restart_sweep",
                                           "multirhs", "poisson64"],
                    default="convdiff128")
@@ -979,6 +982,7 @@ def main():
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     solvers = {f: cb.Solver.from_csr(A, restart=args.restart, fmt=f, arith=args.arith, precond=args.precond,
+                                     spmv_group=args.spmv_group,
                                      adapt=args.adapt, ortho=args.ortho, profile=True)
                for f in fmts}
 

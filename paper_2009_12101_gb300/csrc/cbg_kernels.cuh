@@ -101,14 +101,86 @@ __device__ __forceinline__ bool last_block(unsigned int* counter)
     return is_last;
 }
 
-__device__ __forceinline__ void reduce_norm_parts(const double* part, int np, double& ss, double& mx)
+// The last block's sum of squares and maximum over the per-block pairs (part[2b],
+// part[2b+1]), b < np, computed by every thread of the block (all threads must call it):
+// thread t adds the pairs t, t + blockDim.x, ... in that order, the warps fold their lanes
+// with a fixed shuffle tree and every thread adds the warps' results in warp order, so the
+// result depends only on np and blockDim.x.  The loads of two pairs are issued before
+// they are added: the chain is about np / (2 blockDim.x) memory round trips long.
+__device__ __forceinline__ void block_reduce_norm_parts(const double* part, int np, double& ss, double& mx)
 {
-    // fixed order: lane l sums parts l, l+32, ...; then a fixed shuffle tree
-    const int lane = threadIdx.x & 31;
+    __shared__ double rs[32], rm[32];
+    const int nt = blockDim.x;
     double s = 0.0, m = 0.0;
-    for (int p = lane; p < np; p += 32) { s += __ldcg(part + 2 * p); m = fmax(m, __ldcg(part + 2 * p + 1)); }
-    ss = warp_sum(s);
-    mx = warp_max(m);
+    for (int p0 = threadIdx.x; p0 < np; p0 += 2 * nt) {
+        double vs[2], vm[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int p = p0 + u * nt;
+            vs[u] = p < np ? __ldcg(part + 2 * p) : 0.0;
+            vm[u] = p < np ? __ldcg(part + 2 * p + 1) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+            if (p0 + u * nt < np) {
+                s += vs[u];
+                m = fmax(m, vm[u]);
+            }
+    }
+    s = warp_sum(s);
+    m = warp_max(m);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        rs[warp] = s;
+        rm[warp] = m;
+    }
+    __syncthreads();
+    ss = 0.0;
+    mx = 0.0;
+    for (int w = 0; w < (nt >> 5); w++) {
+        ss += rs[w];
+        mx = fmax(mx, rm[w]);
+    }
+}
+
+// The last block's sums over the per-block partials of nitems items: item i is
+// sum_{b < nb} part[b * ldp + i], handed to emit(i, sum) by lane 0 of the warp that
+// computed it.  Warp w of nwarps takes the items 2w, 2w + 1, then 2(w + nwarps), ...;
+// lane l adds blocks l, l + 32, l + 64, ... in that order and the warp folds its lanes
+// with a fixed shuffle tree (the result depends only on nb).  A lane issues the loads of
+// eight blocks for both items before adding them, so an item costs about nb / 256 memory
+// round trips instead of nb / 32.
+template <class Emit>
+__device__ __forceinline__ void reduce_block_parts(const double* part, long long ldp, int nb, int nitems, int warp,
+                                                   int nwarps, Emit emit)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 2 * warp; i0 < nitems; i0 += 2 * nwarps) {
+        const bool two = i0 + 1 < nitems;
+        double s0 = 0.0, s1 = 0.0;
+        for (int b0 = 0; b0 < nb; b0 += 256) {
+            double v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int b = b0 + lane + 32 * u;
+                const double* q = part + (long long)b * ldp + i0;
+                v0[u] = b < nb ? __ldcg(q) : 0.0;
+                v1[u] = b < nb && two ? __ldcg(q + 1) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (b0 + lane + 32 * u < nb) {
+                    s0 += v0[u];
+                    s1 += v1[u];
+                }
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (lane == 0) {
+            emit(i0, s0);
+            if (two) emit(i0 + 1, s1);
+        }
+    }
 }
 
 // FP64 value of element e of a decoded chunk (scale not applied); exact for every format
@@ -384,15 +456,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_basis_dot(DotArgs a)
         a.part[(long long)blockIdx.x * MAXCOLS + col] = tot;
     }
 
-    if (last_block(a.counter)) {
-        // warp-cooperative, fixed order: lane l adds blocks l, l+32, ...; then a shuffle tree
-        for (int col = warp; col < ncols; col += NW) {
-            double sum = 0.0;
-            for (unsigned int b = lane; b < gridDim.x; b += 32) sum += __ldcg(a.part + (long long)b * MAXCOLS + col);
-            sum = warp_sum(sum);
-            if (lane == 0) a.out[col] = sum * a.scales[col];
-        }
-    }
+    if (last_block(a.counter))
+        reduce_block_parts(a.part, MAXCOLS, gridDim.x, ncols, warp, NW,
+                           [&](int col, double sum) { a.out[col] = sum * a.scales[col]; });
 }
 
 // ====================================================== w_out = w_in + sum_k V_k c_k
@@ -599,9 +665,9 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
             a.part_norm[2 * blockIdx.x + 1] = m;
         }
         if (a.counter) {
-            if (last_block(a.counter) && threadIdx.x < 32) {
+            if (last_block(a.counter)) {
                 double s2, m2;
-                reduce_norm_parts(a.part_norm, gridDim.x, s2, m2);
+                block_reduce_norm_parts(a.part_norm, gridDim.x, s2, m2);
                 if (threadIdx.x == 0) {
                     const double wn = sqrt(s2);
                     a.st->wnorm = wn;
@@ -653,13 +719,21 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
                                         double* ssn)
 {
     DevState* st = a.d.st;
-    const int j = a.j, ldh = st->m + 1;
+    const int j = a.j;
     const int lane = threadIdx.x & 31;
+    // every state field the warp needs, loaded together before anything is written (the
+    // stores below would otherwise order each later load behind them: one L2 round trip each)
+    const int ldh = st->m + 1;
     const int reorth = a.reorth_dev ? *a.reorth_dev : a.reorth;   // did the second pass run
+    const double omega_raw = st->omega, eps_bd = st->eps_bd, target = st->target, bnorm = st->bnorm;
+    const int kcap = st->kcap, record = st->record;
+    const long long iters = st->iters, reorths = st->reorths, hist_cap = st->hist_cap;
+    const double gj = a.d.g[j];
     // back from the power-of-two normalised operator (exact)
     const double hs = a.hexp ? pow2d(a.hexp) : 1.0;
     hn = __dmul_rn(hn, hs);
-    const double omega = __dmul_rn(st->omega, hs);
+    const double omega = __dmul_rn(omega_raw, hs);
+#pragma unroll 4
     for (int i = lane; i <= j + 1; i += 32) {
         double hv = 0.0;
         if (i <= j) {
@@ -718,7 +792,6 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         a.d.sn[j] = s;
         sRo[j] = rr;
         sRo[j + 1] = 0.0;
-        double gj = a.d.g[j];
         double gn = __dmul_rn(-s, gj);
         a.d.g[j + 1] = gn;
         a.d.g[j] = __dmul_rn(c, gj);
@@ -726,15 +799,15 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         st->est = est;
         st->hn = hn;
         st->k = j + 1;
-        st->iters += 1;
-        if (reorth) st->reorths += 1;
+        st->iters = iters + 1;
+        if (reorth) st->reorths = reorths + 1;
         st->reorth_now = 0;          // (every block of this store has read it already)
-        if (st->record && st->iters <= st->hist_cap) a.d.hist[st->iters - 1] = est / st->bnorm;
+        if (record && iters + 1 <= hist_cap) a.d.hist[iters] = est / bnorm;
         int stop = 0;
         if (!isfinite(hn) || !isfinite(omega) || !isfinite(est)) stop = 3;
-        else if (!(hn > st->eps_bd * omega)) stop = 2;
-        else if (est <= st->target) stop = 1;
-        else if (j + 1 >= st->kcap) stop = 4;
+        else if (!(hn > eps_bd * omega)) stop = 2;
+        else if (est <= target) stop = 1;
+        else if (j + 1 >= kcap) stop = 4;
         if (stop) {
             st->stop = stop;
             st->active = 0;
@@ -953,9 +1026,9 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
             a.part[2 * blockIdx.x + 1] = m;
         }
         if (last_block(a.counter)) {
-            if (threadIdx.x < 32) {
+            {
                 double s2, m2;
-                reduce_norm_parts(a.part, gridDim.x, s2, m2);
+                block_reduce_norm_parts(a.part, gridDim.x, s2, m2);
                 if (threadIdx.x == 0) {
                     DevState* st = a.st;
                     if (MODE == SPMV_ARNOLDI) {
@@ -1082,9 +1155,9 @@ __global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
         a.part[2 * blockIdx.x] = t;
         a.part[2 * blockIdx.x + 1] = 0.0;
     }
-    if (last_block(a.counter) && threadIdx.x < 32) {
+    if (last_block(a.counter)) {
         double s2, m2;
-        reduce_norm_parts(a.part, gridDim.x, s2, m2);
+        block_reduce_norm_parts(a.part, gridDim.x, s2, m2);
         if (threadIdx.x == 0) a.st->omega = sqrt(s2);
     }
 }

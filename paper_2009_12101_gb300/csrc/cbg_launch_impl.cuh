@@ -63,8 +63,19 @@ template <int FMT> bool Launcher<FMT>::tma_fits() { return tma_plan<FMT>().stage
 
 template <int FMT> void Launcher<FMT>::dot_tma(int grid, cudaStream_t s, const DotArgs& a, int* fault)
 {
+    // cooperative: the kernel's blocks meet at a grid barrier before the cross-block sum
     const TmaPlan& p = tma_plan<FMT>();
-    k_basis_dot_tma<FMT><<<grid, DOT_THREADS, p.smem, s>>>(a, p.stages, fault);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(DOT_THREADS);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_basis_dot_tma<FMT>, a, p.stages, fault);
 }
 
 template <int FMT> void Launcher<FMT>::store(int grid, cudaStream_t s, const StoreArgs& a)

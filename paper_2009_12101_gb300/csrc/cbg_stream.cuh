@@ -1,10 +1,12 @@
 // cbg_stream.cuh -- the basis dot product h = V^T w (the CGS projection and its re-orthogonalisation, Fig. 1) with the
 // compressed basis staged in shared memory by bulk copies (TMA).
 //
-// One block per SM: sixteen consumer warps and one producer warp.  A block owns a
-// contiguous range of row tiles (TILE = 8 row groups x 32 lanes x E rows, E = 16 / bytes
-// per code, so one tile of one column is 4 KiB of codes).  The producer walks the
-// block's work items -- (column group, tile), group-major -- and for each one fills a
+// One block per SM: sixteen consumer warps and one producer warp.  The work items are
+// the (column group, row tile) pairs, numbered group-major (TILE = 8 row groups x 32
+// lanes x E rows, E = 16 / bytes per code, so one tile of one column is 4 KiB of codes),
+// and a block owns a contiguous range of items, so the blocks' shares differ by at most
+// one item (a block may start or end inside a column group).  The producer walks the
+// block's items and for each one fills a
 // stage of a ring in shared memory with one bulk copy per column (4 KiB each, L2
 // evict-first) plus the tile of w as FP32 hi and lo planes; completion is counted in
 // bytes on the stage's "full" mbarrier.  Consumer warp w takes row group w % 8 and half
@@ -46,17 +48,50 @@ inline int tma_stages(int stage_bytes, int static_bytes)
 }
 inline size_t tma_smem_bytes(int stages, int stage_bytes) { return (size_t)stages * stage_bytes + 2 * (size_t)stages * 8; }
 
-// block's contiguous tile range
-__device__ __forceinline__ void block_tiles(long long ntiles, long long& tb, long long& te)
+// the block's contiguous range [ib, ie) of nitems work items
+__device__ __forceinline__ void block_items(long long nitems, long long& ib, long long& ie)
 {
-    tb = (long long)blockIdx.x * ntiles / gridDim.x;
-    te = ((long long)blockIdx.x + 1) * ntiles / gridDim.x;
+    ib = (long long)blockIdx.x * nitems / gridDim.x;
+    ie = ((long long)blockIdx.x + 1) * nitems / gridDim.x;
 }
 
 __device__ __forceinline__ void record_fault(DevState* st, int* fault)
 {
     if (fault) atomicExch(fault, FAULT_TIMEOUT);
     else if (st) atomicExch(&st->fault, FAULT_TIMEOUT);
+}
+
+// Barrier of all blocks of a cooperative launch on one counter word: bits 0..30 count the
+// arrivals, bit 31 is the sense, flipped by the last arrival (which also zeroes the
+// count), so the word is ready for the next launch as it is left.  Thread 0 of each
+// block arrives and waits (bounded: false when the wait gave up); the fences order the
+// block's writes before its arrival and the other blocks' writes before its departure.
+__device__ __forceinline__ bool grid_barrier(unsigned int* cnt, long long limit)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned sense = *(volatile unsigned*)cnt & 0x80000000u;
+        const unsigned old = atomicAdd(cnt, 1u);
+        int good = 1;
+        if ((old & 0x7FFFFFFFu) == gridDim.x - 1) {
+            atomicExch(cnt, sense ^ 0x80000000u);
+        } else {
+            const long long t0 = clock64();
+            while ((*(volatile unsigned*)cnt & 0x80000000u) == sense) {
+                if (clock64() - t0 > limit) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
 }
 
 // position in the ring: stage index and the parity of its current use
@@ -94,18 +129,17 @@ template <int E> __device__ __forceinline__ void load_floats(const float* p, flo
 // (bounded) until every issued copy has landed, so no copy outlives the block.
 template <int COLB>
 __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes, int stages, uint64_t* full,
-                                            uint64_t* empty, long long tb, long long te, int ncols, int cg,
-                                            const unsigned char* V, long long ldb, const float* wsrc, long long wld,
-                                            int tile_rows, int* failed, long long limit, bool withhold)
+                                            uint64_t* empty, long long ib, long long ie, long long ntiles, int ncols,
+                                            int cg, const unsigned char* V, long long ldb, const float* wsrc,
+                                            long long wld, int tile_rows, int* failed, long long limit, bool withhold)
 {
     const int lane = threadIdx.x & 31;
-    const int ngroups = (ncols + cg - 1) / cg;
-    const long long nitems = (te - tb) * ngroups;
+    const long long nitems = ie - ib;
     const uint64_t pol = l2_evict_first_policy();
     const unsigned wplane = (unsigned)tile_rows * 4u;
     Ring rg;
-    long long t = tb, it = 0;
-    int g = 0;
+    int g = ntiles > 0 ? (int)(ib / ntiles) : 0;
+    long long t = ib - (long long)g * ntiles, it = 0;
     for (; it < nitems; it++) {
         const int c0 = g * cg;
         const int nc = ncols - c0 < cg ? ncols - c0 : cg;
@@ -123,7 +157,7 @@ __device__ __forceinline__ void tma_produce(unsigned char* ring, int stage_bytes
         }
         __syncwarp();
         rg.next(stages);
-        if (++t == te) { t = tb; g++; }
+        if (++t == ntiles) { t = 0; g++; }
     }
     // drain: walk back over the last min(it, stages) items, the newest use of each stage
     const long long nd = it < stages ? it : stages;
@@ -198,9 +232,10 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
     const int ncols = a.ncols_dev ? *a.ncols_dev : a.ncols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
-    long long tb, te;
-    block_tiles(a.nrows / G::TILE, tb, te);
+    const long long ntiles = a.nrows / G::TILE;
     const int ngroups = (ncols + CG - 1) / CG;
+    long long ib, ie;
+    block_items(ntiles * ngroups, ib, ie);
 
     if (threadIdx.x == 0) {
         failed = 0;
@@ -215,17 +250,21 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
 
     if (warp == DOT_CW) {
         int f = 0;
-        tma_produce<G::COLB>(ring, G::STAGE_DOT, stages, full, empty, tb, te, ncols, CG, a.V, a.ldb, a.wdf, a.nrows,
-                             G::TILE, &f, limit, a.withhold != 0);
+        tma_produce<G::COLB>(ring, G::STAGE_DOT, stages, full, empty, ib, ie, ntiles, ncols, CG, a.V, a.ldb, a.wdf,
+                             a.nrows, G::TILE, &f, limit, a.withhold != 0);
         if (f) failed = 1;
-    } else if (te > tb) {
+    } else if (ie > ib) {
         const int rgp = warp % TMA_CW, q0 = (warp / TMA_CW) * CGW;
         const int r = (rgp * 32 + lane) * E;      // first row of this lane within a tile
         bool bad = false;
         Ring rg;
-        for (int g = 0; g < ngroups; g++) {
+        const int gb = (int)(ib / ntiles), ge = (int)((ie - 1) / ntiles) + 1;   // the block's column groups
+        for (int g = gb; g < ge; g++) {
             const int c0 = g * CG;
             const int nc = ncols - c0 < CG ? ncols - c0 : CG;
+            // this block's tiles of group g
+            const long long tb = ib > (long long)g * ntiles ? ib - (long long)g * ntiles : 0;
+            const long long te = ie < (long long)(g + 1) * ntiles ? ie - (long long)g * ntiles : ntiles;
             float2 S2[CGW / 2], C2[CGW / 2];
 #pragma unroll
             for (int q = 0; q < CGW / 2; q++) { S2[q] = make_float2(0.f, 0.f); C2[q] = make_float2(0.f, 0.f); }
@@ -268,13 +307,45 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
     __syncthreads();
     if (failed && threadIdx.x == 0) record_fault(nullptr, fault);
     for (int col = threadIdx.x; col < ncols; col += DOT_THREADS) a.part[(long long)blockIdx.x * MAXCOLS + col] = red_tot[col];
-    if (last_block(a.counter)) {
-        for (int col = warp; col < ncols; col += DOT_CW + 1) {
-            double sum = 0.0;
-            for (unsigned int b = lane; b < gridDim.x; b += 32) sum += __ldcg(a.part + (long long)b * MAXCOLS + col);
-            sum = warp_sum(sum);
-            if (lane == 0) a.out[col] = sum * a.scales[col];
+    // Grid barrier (the kernel is launched cooperatively: every block is resident), then
+    // block b adds the partials of the columns b, b + gridDim.x, ...: one load per thread
+    // and column, one warp shuffle tree per warp, the warps' sums in warp order.  The
+    // cross-block sum is spread over all SMs instead of one last block, whose FP64 pipe
+    // (a few FP64 operations per clock per SM on GB300) and serial L2 round trips would
+    // otherwise add tens of microseconds to a launch.
+    if (!grid_barrier(a.counter, limit)) {
+        if (threadIdx.x == 0) record_fault(nullptr, fault);
+        return;
+    }
+    __shared__ double wsum_sh[DOT_CW + 1][4];
+    const int nb = gridDim.x;
+    for (int c0 = blockIdx.x; c0 < ncols; c0 += 4 * nb) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = threadIdx.x; t < nb; t += DOT_THREADS) {   // a thread adds blocks t, t + 544, ...
+            double q[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int col = c0 + k * nb;
+                q[k] = col < ncols ? __ldcg(a.part + (long long)t * MAXCOLS + col) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] += q[k];
         }
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = warp_sum(v[k]);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; k++) wsum_sh[warp][k] = v[k];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            const int col = c0 + threadIdx.x * nb;
+            if (col < ncols) {
+                double sum = 0.0;
+                for (int w = 0; w < DOT_CW + 1; w++) sum += wsum_sh[w][threadIdx.x];
+                a.out[col] = sum * a.scales[col];
+            }
+        }
+        __syncthreads();
     }
 }
 

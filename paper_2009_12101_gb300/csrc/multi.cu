@@ -175,16 +175,11 @@ __global__ void __launch_bounds__(MT, 1) k_dot_multi(MultiArgs a)
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ncols * KR; i += MT) a.part[(long long)blockIdx.x * ncols * KR + i] = tot[i];
-    if (last_block(a.counter)) {
-        for (int i = warp; i < ncols * a.k; i += MNW) {
-            const int col = i / a.k, r = i - col * a.k;
-            double sum = 0.0;
-            for (unsigned int b = lane; b < gridDim.x; b += 32)
-                sum += __ldcg(a.part + (long long)b * ncols * KR + col * KR + r);
-            sum = warp_sum(sum);
-            if (lane == 0) a.H[(long long)col * a.ldh + r] = sum * a.scales[col];
-        }
-    }
+    if (last_block(a.counter))   // items col * KR + r; the partials of r >= k are zero and not kept
+        reduce_block_parts(a.part, (long long)ncols * KR, gridDim.x, ncols * KR, warp, MNW, [&](int i, double sum) {
+            const int col = i / KR, r = i - col * KR;
+            if (r < a.k) a.H[(long long)col * a.ldh + r] = sum * a.scales[col];
+        });
 }
 
 template <int FMT, int KR> void launch_multi(int grid, cudaStream_t s, const MultiArgs& a)

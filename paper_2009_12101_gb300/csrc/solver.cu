@@ -1381,11 +1381,15 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) TRY(CBG_ERR_CUDA);
         // the shortest of 5 single launches after one warm-up launch (a single launch
-        // is 10-100 us here: the minimum is far less noisy than a mean)
+        // is 10-100 us here: the minimum is far less noisy than a mean); before each, a
+        // write of up to 256 MiB of the (still zero) basis evicts the matrix from L2, as
+        // the basis products do between two SpMVs of a solve
+        const size_t flush = std::min<size_t>(vbytes, size_t(256) << 20);
         auto time_min = [&](auto&& launch, float& best_ms) -> bool {
             launch();
             best_ms = 1e30f;
             for (int rep = 0; rep < 5; rep++) {
+                if (cudaMemsetAsync(h->V, 0, flush, h->stream) != cudaSuccess) return false;
                 cudaEventRecord(t0, h->stream);
                 launch();
                 cudaEventRecord(t1, h->stream);
