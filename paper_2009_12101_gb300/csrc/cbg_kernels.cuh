@@ -40,8 +40,9 @@ struct DevState {
     int last_k;           // columns of the previous cycle (set when a cycle starts)
     int fault;            // nonzero: a pipelined kernel gave up waiting (FAULT_TIMEOUT)
     double wnorm, wmax;   // ||w||_2 and ||w||_inf of the orthogonalised w (last axpy block)
-    int reorth_now;       // conditional mode: the current step's second pass runs (set by the
-                          // first pass's last axpy block, cleared by the store's finalize)
+    int reorth_now;       // conditional mode: the current step's second pass runs (written at
+                          // every step by the first pass's last axpy block, cleared when a
+                          // cycle starts)
     int pad_state;
 };
 
@@ -705,7 +706,7 @@ struct StoreArgs {
 };
 
 
-// Executed by warp 0 of the store kernel's last block.  The column, the previous
+// Executed by warp 0 of the store kernel's block 0.  The column, the previous
 // rotations and the coefficients are staged in shared memory by the whole warp first.
 //
 // Applying the j previous rotations to the new column is a first-order linear recurrence
@@ -801,7 +802,6 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         st->k = j + 1;
         st->iters = iters + 1;
         if (reorth) st->reorths = reorths + 1;
-        st->reorth_now = 0;          // (every block of this store has read it already)
         if (record && iters + 1 <= hist_cap) a.d.hist[iters] = est / bnorm;
         int stop = 0;
         if (!isfinite(hn) || !isfinite(omega) || !isfinite(est)) stop = 3;
@@ -838,12 +838,22 @@ __global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
         sh_ep = enc_params(FMT, __dmul_rn(mx, inv));
     }
     __syncthreads();
+    // Mode 0: block 0 completes the Hessenberg column and the Givens update (a serial
+    // chain of FP64 operations on one warp) while blocks 1.. encode the new basis vector:
+    // the chain needs only h, u and ||w||, all known when the kernel starts.  Block 0 is
+    // dispatched first, so it never waits for an encoding block to leave the SM.
+    if (a.mode == 0 && blockIdx.x == 0) {
+        if (threadIdx.x < 32) arnoldi_finalize(a, sh_hn, sR, sRo, scs, ssn);
+        return;
+    }
+    const int eb = a.mode == 0 ? (int)blockIdx.x - 1 : (int)blockIdx.x;     // encoding block
+    const int neb = a.mode == 0 ? (int)gridDim.x - 1 : (int)gridDim.x;
     const double inv = sh_inv;
     const EncParams ep = sh_ep;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
+    if (eb == 0 && threadIdx.x == 0) a.d.scales[a.col] = ep.scale;
     const double* wsrc = (a.reorth_dev && *a.reorth_dev == 0) ? a.w_alt : a.w;
-    const long long stride = (long long)gridDim.x * THREADS;
-    for (long long i0 = (long long)blockIdx.x * THREADS + threadIdx.x; i0 < a.n; i0 += 4 * stride) {
+    const long long stride = (long long)neb * THREADS;
+    for (long long i0 = (long long)eb * THREADS + threadIdx.x; i0 < a.n; i0 += 4 * stride) {
         double wv[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {   // four loads in flight per thread
@@ -856,9 +866,6 @@ __global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
             if (i < a.n) encode_store<FMT>(a.Vcol, i, __dmul_rn(wv[q], inv), ep);
         }
     }
-    // The Hessenberg / Givens work is a serial chain of FP64 operations; it runs in the
-    // last block to finish, when no other block competes for the SM's narrow FP64 pipe.
-    if (a.mode == 0 && last_block(a.counter) && threadIdx.x < 32) arnoldi_finalize(a, sh_hn, sR, sRo, scs, ssn);
 }
 
 // ======================================================= SpMV with on-the-fly decode

@@ -80,7 +80,8 @@ template <int FMT> void Launcher<FMT>::dot_tma(int grid, cudaStream_t s, const D
 
 template <int FMT> void Launcher<FMT>::store(int grid, cudaStream_t s, const StoreArgs& a)
 {
-    k_store<FMT><<<grid, THREADS, 0, s>>>(a);
+    // mode 0: at least two blocks (block 0 runs the Givens update, the others encode)
+    k_store<FMT><<<a.mode == 0 ? (grid > 1 ? grid : 2) : grid, THREADS, 0, s>>>(a);
 }
 
 template <int FMT>
