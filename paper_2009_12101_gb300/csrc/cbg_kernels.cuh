@@ -481,7 +481,8 @@ struct AxpyArgs {
     const double* coef;       // device [ncols]
     double sign;
     const double* w_in;
-    double* w_out;
+    double* w_out;            // EPI_SUB, DF32: may be null when wdf_out is set (only the split
+                              // copy is written; no norms then, counter must be null)
     const double* dinv;       // Jacobi (EPI_XUPD), may be null
     long long nrows;          // ld
     long long n;              // true rows (norms exclude padding)
@@ -625,6 +626,15 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                     }
                     df_add(S[e], C[e], wh, wl);
                 }
+                if (EPI == EPI_SUB && !a.w_out) {
+                    // only the split copy is wanted (the first CGS pass when the second
+                    // always runs): the renormalised pair itself, no FP64 operation, no norms
+                    float h, l;
+                    two_sum(S[e], C[e], h, l);
+                    a.wdf_out[i] = h;
+                    a.wdf_out[a.nrows + i] = l;
+                    continue;
+                }
                 acc = df_to_double(S[e], C[e]);
             } else {
                 acc = D[e];
@@ -638,7 +648,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                     a.wdf_out[i] = h;
                     a.wdf_out[a.nrows + i] = l;
                 }
-                if (i < a.n) {
+                if (a.counter && i < a.n) {           // the norms only when a last block reads them
                     ss = __fma_rn(acc, acc, ss);
                     unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & 0x7FFFFFFFFFFFFFFFull;
                     mxb = ab > mxb ? ab : mxb;
@@ -654,6 +664,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
         }
     }
     if constexpr (EPI == EPI_SUB) {
+        if (!a.counter) return;
         ss = warp_sum(ss);
         double mx = warp_max(__longlong_as_double((long long)mxb));
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -665,7 +676,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
             a.part_norm[2 * blockIdx.x] = s;
             a.part_norm[2 * blockIdx.x + 1] = m;
         }
-        if (a.counter) {
+        {
             if (last_block(a.counter)) {
                 double s2, m2;
                 block_reduce_norm_parts(a.part_norm, gridDim.x, s2, m2);
@@ -955,6 +966,8 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     float ssS = 0.f, ssC = 0.f, xsh = 1.f, xsl = 0.f;    // double-float rows: ||y||^2, scale
     const bool xsplit = dfrows && xs != 1.0;
     if (xsplit) split_f64(xs, xsh, xsl);
+    const float* vlo = dfrows ? a.valdf + a.nnz : nullptr;       // lo plane of the values
+    float* ylo = dfrows ? a.ydf + a.ydf_ld : nullptr;            // lo plane of w
     for (long long row = gid;; row += ngroups) {
         const bool valid = row < a.n;
         if constexpr (GROUP > 1) {
@@ -967,7 +980,7 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
         if (dfrows) {
             float S = 0.f, C = 0.f;
             for (int p = p0 + lane_g; p < p1; p += GROUP) {
-                const float vh = a.valdf[p], vl = a.valdf[a.nnz + p];
+                const float vh = a.valdf[p], vl = vlo[p];
                 const int cp = a.col[p];
                 if (!col_ok(cp, a.n, a.st)) continue;
                 float xh, xl;
@@ -998,7 +1011,7 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
                     two_sum(p, e, hi, lo);
                 }
                 a.ydf[row] = hi;
-                a.ydf[a.ydf_ld + row] = lo;
+                ylo[row] = lo;
                 const float p = __fmul_rn(hi, hi);           // ||y||^2 in double-float
                 float e = __fmaf_rn(hi, hi, -p);
                 e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);

@@ -844,6 +844,10 @@ void enqueue_step(cbg_handle* h, int j)
         // and its last block decides on the device whether the second pass runs
         xa.counter = reorth && !cond ? nullptr : h->d.counters + 5;
         xa.wdf_out = reorth ? wdf : nullptr;                  // the second dot reads w1 split
+        // DF32, second pass always: w1 is read only as its split planes (by the second dot
+        // and the second axpy), so the first axpy writes nothing else
+        const bool planes_only = reorth && !cond && wdf;
+        if (planes_only) xa.w_out = nullptr;
         if (cond) {
             xa.reorth_flag = &h->d.st->reorth_now;
             xa.eta = h->opt.eta;
@@ -859,8 +863,8 @@ void enqueue_step(cbg_handle* h, int j)
             da.active = gate;
             launch(h, 0, pass_bytes, run_dot);
             xa.coef = h->d.u;
-            xa.w_in = h->w1;
-            xa.wdf_in = nullptr;
+            xa.w_in = planes_only ? nullptr : h->w1;
+            xa.wdf_in = planes_only ? wdf : nullptr;
             xa.w_out = h->w2;
             xa.wdf_out = nullptr;
             xa.counter = h->d.counters + 5;
