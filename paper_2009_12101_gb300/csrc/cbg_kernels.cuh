@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
     }
     __syncthreads();
 
-    double ss = 0.0;             // epilogue partials: sum of squares (FP64) and
+    double ss = 0.0;             // epilogue partials: sum of squares (FP64; double-float in
+    float ssS = 0.f, ssC = 0.f;  // (ssS, ssC) with DF32 arithmetic) and
     unsigned long long mxb = 0;  // max |w| as the bit pattern of a non-negative double
     // warp segments of 32 chunks (32*E rows), dealt round-robin in SM-spread order
     const long long nseg = a.nrows / (32 * E);
@@ -635,7 +636,23 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                     a.wdf_out[a.nrows + i] = l;
                     continue;
                 }
-                acc = df_to_double(S[e], C[e]);
+                if constexpr (EPI == EPI_SUB) {
+                    // sum of squares in double-float on the FP32 pipe (GB300's FP64 pipe
+                    // runs at 1/64 of it): (h + l)^2 = h^2 + 2hl, h^2 exact as a pair
+                    float h, l;
+                    two_sum(S[e], C[e], h, l);
+                    if (a.counter && i < a.n) {
+                        const float p = __fmul_rn(h, h);
+                        float q = __fmaf_rn(h, h, -p);
+                        q = __fmaf_rn(__fadd_rn(h, h), l, q);
+                        const float t = __fadd_rn(ssS, p), bb = __fsub_rn(t, ssS);
+                        ssC = __fadd_rn(ssC, __fadd_rn(__fadd_rn(__fsub_rn(ssS, __fsub_rn(t, bb)), __fsub_rn(p, bb)), q));
+                        ssS = t;
+                    }
+                    acc = df_to_double(h, l);
+                } else {
+                    acc = df_to_double(S[e], C[e]);
+                }
             } else {
                 acc = D[e];
                 if constexpr (EPI == EPI_SUB) acc = __dadd_rn(a.w_in[i], acc);
@@ -649,7 +666,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                     a.wdf_out[a.nrows + i] = l;
                 }
                 if (a.counter && i < a.n) {           // the norms only when a last block reads them
-                    ss = __fma_rn(acc, acc, ss);
+                    if constexpr (ARITH != ARITH_DF32) ss = __fma_rn(acc, acc, ss);
                     unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & 0x7FFFFFFFFFFFFFFFull;
                     mxb = ab > mxb ? ab : mxb;
                 }
@@ -665,6 +682,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
     }
     if constexpr (EPI == EPI_SUB) {
         if (!a.counter) return;
+        if constexpr (ARITH == ARITH_DF32) ss = df_to_double(ssS, ssC);
         ss = warp_sum(ss);
         double mx = warp_max(__longlong_as_double((long long)mxb));
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -799,7 +817,11 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         double rr = hypot(r0, hn);
         double c, s;
         if (rr == 0.0) { c = 1.0; s = 0.0; }
-        else { c = r0 / rr; s = hn / rr; }
+        else {                               // one FP64 division on the critical chain, not two
+            const double ri = 1.0 / rr;
+            c = __dmul_rn(r0, ri);
+            s = __dmul_rn(hn, ri);
+        }
         a.d.cs[j] = c;
         a.d.sn[j] = s;
         sRo[j] = rr;
@@ -835,28 +857,28 @@ __global__ void __launch_bounds__(THREADS, 4) k_store(StoreArgs a)
 {
     DevState* st = a.d.st;
     if (st->active == 0) return;
-    __shared__ double sh_inv, sh_hn;
+    __shared__ double sh_inv;
     __shared__ EncParams sh_ep;
     __shared__ double sR[MAXCOLS + 1], sRo[MAXCOLS + 1], scs[MAXCOLS], ssn[MAXCOLS];
+    // Mode 0: block 0 completes the Hessenberg column and the Givens update (a serial
+    // chain of FP64 operations on one warp) while blocks 1.. encode the new basis vector:
+    // the chain needs only h, u and ||w||, all known when the kernel starts, so its warp
+    // starts at once.  Block 0 is dispatched first, so it never waits for an encoding
+    // block to leave the SM.
+    if (a.mode == 0 && blockIdx.x == 0) {
+        if (threadIdx.x < 32) arnoldi_finalize(a, st->wnorm, sR, sRo, scs, ssn);
+        return;
+    }
     if (threadIdx.x == 0) {
         // norms of the vector to store: the residual (first vector of a cycle) or the
         // orthogonalised w, both finalised by the last block of the producing kernel
         const double hn = a.mode == 1 ? st->beta : st->wnorm;
         const double mx = a.mode == 1 ? st->rinf : st->wmax;
         const double inv = 1.0 / hn;
-        sh_hn = hn;
         sh_inv = inv;
         sh_ep = enc_params(FMT, __dmul_rn(mx, inv));
     }
     __syncthreads();
-    // Mode 0: block 0 completes the Hessenberg column and the Givens update (a serial
-    // chain of FP64 operations on one warp) while blocks 1.. encode the new basis vector:
-    // the chain needs only h, u and ||w||, all known when the kernel starts.  Block 0 is
-    // dispatched first, so it never waits for an encoding block to leave the SM.
-    if (a.mode == 0 && blockIdx.x == 0) {
-        if (threadIdx.x < 32) arnoldi_finalize(a, sh_hn, sR, sRo, scs, ssn);
-        return;
-    }
     const int eb = a.mode == 0 ? (int)blockIdx.x - 1 : (int)blockIdx.x;     // encoding block
     const int neb = a.mode == 0 ? (int)gridDim.x - 1 : (int)gridDim.x;
     const double inv = sh_inv;
