@@ -139,6 +139,12 @@ __device__ __forceinline__ void df_add(float& aS, float& aC, float bS, float bC)
     fast_two_sum(s, e, aS, aC);
 }
 
+// The hardware conversions between FP32 and FP64 run on GB300's narrow FP64 pipe.  The
+// helpers below convert in integer operations and keep the hardware instruction only
+// for rare inputs, behind a call that the compiler cannot turn into predicated code
+// (a predicated-off FP64-pipe instruction still occupies the pipe).
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return __double2float_rn(x); }
+
 // Split an FP64 value into hi + lo FP32 with integer operations only (the FP64 pipe of
 // GB300 is ~70x slower than FP32).  hi = x truncated to 24 significant bits (exact),
 // lo = the remaining 29 significand bits rounded to 24 bits, so hi + lo = x with a
@@ -166,25 +172,34 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo)
         hi = __uint_as_float(sign);
         lo = 0.0f;
     } else {
-        hi = __double2float_rn(x);
+        hi = f64_to_f32_hw(x);
         lo = 0.0f;
     }
 }
 
-// Exact FP32 -> FP64 conversion with integer operations (the F2F instruction runs on
-// GB300's slow FP64 pipe).  Normal numbers and zeros take the integer path; subnormal,
-// infinite and NaN inputs fall back to the hardware conversion.
+// Exact FP32 -> FP64 conversion, every input in integer operations (normal numbers,
+// zeros, subnormals normalised with a leading-zero count, infinities and NaNs).
 __device__ __forceinline__ double f32_to_f64_exact(float f)
 {
     const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFFu;
-    if (e - 1u < 254u) {
-        const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-        const unsigned int lo = (u & 7u) << 29;
-        return __hiloint2double((int)hi, (int)lo);
+    const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    unsigned int hi, lo;
+    if (e - 1u < 254u) {                       // normal
+        hi = sign | ((e + 896u) << 20) | (m >> 3);
+        lo = (m & 7u) << 29;
+    } else if (e == 255u) {                    // infinity, NaN (payload kept)
+        hi = sign | 0x7FF00000u | (m >> 3);
+        lo = (m & 7u) << 29;
+    } else if (m == 0u) {                      // zero
+        hi = sign;
+        lo = 0u;
+    } else {                                   // subnormal m * 2^-149: leading one to bit 23
+        const unsigned int sh = (unsigned int)__clz(m) - 8u;
+        const unsigned int mn = (m << sh) & 0x7FFFFFu;
+        hi = sign | ((897u - sh) << 20) | (mn >> 3);
+        lo = (mn & 7u) << 29;
     }
-    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    return (double)f;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // FP64 -> FP32 with round-to-nearest-even, in integer operations when the result is a
@@ -204,7 +219,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x)
         return __uint_as_float(b | sign);
     }
     if ((u << 1) == 0ull) return __uint_as_float(sign);       // +-0
-    return __double2float_rn(x);
+    return f64_to_f32_hw(x);
 }
 
 // hi + lo rounded once to FP64: both widened exactly with integer operations, then one

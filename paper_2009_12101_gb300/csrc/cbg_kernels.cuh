@@ -11,6 +11,8 @@
 #include "cbg_device.cuh"
 #include "cbg_tma.cuh"
 
+#include <type_traits>
+
 namespace cbg {
 
 constexpr int THREADS = 256;
@@ -519,172 +521,195 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
 
     double ss = 0.0;             // epilogue partials: sum of squares (FP64; double-float in
     float ssS = 0.f, ssC = 0.f;  // (ssS, ssC) with DF32 arithmetic) and
-    unsigned long long mxb = 0;  // max |w| as the bit pattern of a non-negative double
+    unsigned int mxh = 0, mxl = 0;   // max |w| as the bit pattern of a non-negative double
+                                     // (high and low words, compared with 32-bit operations)
     // warp segments of 32 chunks (32*E rows), dealt round-robin in SM-spread order
     const long long nseg = a.nrows / (32 * E);
     const long long nwt = (long long)gridDim.x * (THREADS / 32);
-    for (long long sg = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; sg < nseg; sg += nwt) {
-        const long long row0 = (sg * 32 + (threadIdx.x & 31)) * E;
-        const unsigned char* base = a.V + row0 * BS;
-        float2 S2[E / 2], C2[E / 2];     // rows (2i, 2i+1) on the packed FP32x2 pipe
-        double D[E];
+    // The segment loop, compiled per epilogue case so that no case carries the others'
+    // instructions as predicated code (on GB300 a predicated-off FP64-pipe instruction
+    // still occupies the narrow FP64 pipe): M = 1 the split planes only, M = 2 w and its
+    // norms without the split copy (the final CGS pass), M = 0 any combination.
+    auto segments = [&](auto mode_tag) {
+        constexpr int M = decltype(mode_tag)::value;
+        (void)M;
+        for (long long sg = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; sg < nseg; sg += nwt) {
+            const long long row0 = (sg * 32 + (threadIdx.x & 31)) * E;
+            const unsigned char* base = a.V + row0 * BS;
+            // rows of this lane below n (the norms exclude the padding), as a 32-bit count
+            const int nvalid = a.n - row0 >= E ? E : (a.n > row0 ? (int)(a.n - row0) : 0);
+            (void)nvalid;
+            float2 S2[E / 2], C2[E / 2];     // rows (2i, 2i+1) on the packed FP32x2 pipe
+            double D[E];
 #pragma unroll
-        for (int e = 0; e < E / 2; e++) { S2[e] = make_float2(0.f, 0.f); C2[e] = make_float2(0.f, 0.f); }
+            for (int e = 0; e < E / 2; e++) { S2[e] = make_float2(0.f, 0.f); C2[e] = make_float2(0.f, 0.f); }
 #pragma unroll
-        for (int e = 0; e < E; e++) D[e] = 0.0;
-        auto column = [&](const uint4& raw, float2 c) {
-            Chunk<FMT> ch;
-            decode_chunk<FMT>(raw, ch);
-            if constexpr (ARITH == ARITH_DF32) {
-                const float2 ch2 = make_float2(c.x, c.x), nch2 = make_float2(-c.x, -c.x), cl2 = make_float2(c.y, c.y);
+            for (int e = 0; e < E; e++) D[e] = 0.0;
+            auto column = [&](const uint4& raw, float2 c) {
+                Chunk<FMT> ch;
+                decode_chunk<FMT>(raw, ch);
+                if constexpr (ARITH == ARITH_DF32) {
+                    const float2 ch2 = make_float2(c.x, c.x), nch2 = make_float2(-c.x, -c.x), cl2 = make_float2(c.y, c.y);
 #pragma unroll
-                for (int e = 0; e < E; e += 2) {
-                    if constexpr (SingleFloat<FMT>::value)
-                        df2_mac(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]), ch2, nch2, cl2);
-                    else
-                        df2_mac2(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]),
-                                 make_float2(ch.vl[e], ch.vl[e + 1]), ch2, nch2, cl2);
+                    for (int e = 0; e < E; e += 2) {
+                        if constexpr (SingleFloat<FMT>::value)
+                            df2_mac(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]), ch2, nch2, cl2);
+                        else
+                            df2_mac2(S2[e / 2], C2[e / 2], make_float2(ch.vh[e], ch.vh[e + 1]),
+                                     make_float2(ch.vl[e], ch.vl[e + 1]), ch2, nch2, cl2);
+                    }
+                } else {
+                    const double cd = *reinterpret_cast<double*>(&c);
+#pragma unroll
+                    for (int e = 0; e < E; e++) D[e] = __fma_rn(chunk_f64<FMT>(raw, ch, e), cd, D[e]);
+                }
+            };
+            int k = 0;
+            if constexpr (ARITH == ARITH_DF32 && BS == 4) {
+                // 4-byte codes (latency-bound): two groups of four columns, software-pipelined,
+                // so the next group's loads are in flight while the current group is
+                // accumulated (measured 3 % faster for f32; slower for the FMA-bound 2-byte codes)
+                constexpr int H = 4;
+                uint4 ra[H], rb[H];
+                if (H <= ncols) {
+#pragma unroll
+                    for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)q * a.ldb);
+                }
+                for (; k + 2 * H <= ncols; k += 2 * H) {
+#pragma unroll
+                    for (int q = 0; q < H; q++) rb[q] = ldg_stream(base + (long long)(k + H + q) * a.ldb);
+#pragma unroll
+                    for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
+#pragma unroll
+                    for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                    if (k + 3 * H <= ncols) {
+#pragma unroll
+                        for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)(k + 2 * H + q) * a.ldb);
+                    }
+#pragma unroll
+                    for (int q = 0; q < H; q++) column(rb[q], cs[k + H + q]);
+#pragma unroll
+                    for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                }
+                if (k + H <= ncols) {             // a last full group of four (already loaded)
+#pragma unroll
+                    for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
+#pragma unroll
+                    for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                    k += H;
                 }
             } else {
-                const double cd = *reinterpret_cast<double*>(&c);
+                for (; k + U <= ncols; k += U) {
+                    uint4 raw[U];
 #pragma unroll
-                for (int e = 0; e < E; e++) D[e] = __fma_rn(chunk_f64<FMT>(raw, ch, e), cd, D[e]);
-            }
-        };
-        int k = 0;
-        if constexpr (ARITH == ARITH_DF32 && BS == 4) {
-            // 4-byte codes (latency-bound): two groups of four columns, software-pipelined,
-            // so the next group's loads are in flight while the current group is
-            // accumulated (measured 3 % faster for f32; slower for the FMA-bound 2-byte codes)
-            constexpr int H = 4;
-            uint4 ra[H], rb[H];
-            if (H <= ncols) {
+                    for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
 #pragma unroll
-                for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)q * a.ldb);
-            }
-            for (; k + 2 * H <= ncols; k += 2 * H) {
+                    for (int q = 0; q < U; q++) {
+                        column(raw[q], cs[k + q]);
+                        if constexpr (ARITH == ARITH_DF32) {
+                            if ((q & 3) == 3) {
 #pragma unroll
-                for (int q = 0; q < H; q++) rb[q] = ldg_stream(base + (long long)(k + H + q) * a.ldb);
-#pragma unroll
-                for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
-#pragma unroll
-                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
-                if (k + 3 * H <= ncols) {
-#pragma unroll
-                    for (int q = 0; q < H; q++) ra[q] = ldg_stream(base + (long long)(k + 2 * H + q) * a.ldb);
-                }
-#pragma unroll
-                for (int q = 0; q < H; q++) column(rb[q], cs[k + H + q]);
-#pragma unroll
-                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
-            }
-            if (k + H <= ncols) {             // a last full group of four (already loaded)
-#pragma unroll
-                for (int q = 0; q < H; q++) column(ra[q], cs[k + q]);
-#pragma unroll
-                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
-                k += H;
-            }
-        } else {
-            for (; k + U <= ncols; k += U) {
-                uint4 raw[U];
-#pragma unroll
-                for (int q = 0; q < U; q++) raw[q] = ldg_stream(base + (long long)(k + q) * a.ldb);
-#pragma unroll
-                for (int q = 0; q < U; q++) {
-                    column(raw[q], cs[k + q]);
-                    if constexpr (ARITH == ARITH_DF32) {
-                        if ((q & 3) == 3) {
-#pragma unroll
-                            for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                                for (int e = 0; e < E / 2; e++) df2_renorm(S2[e], C2[e]);
+                            }
                         }
                     }
                 }
             }
-        }
-        for (; k < ncols; k++) column(ldg_stream(base + (long long)k * a.ldb), cs[k]);
-        float S[E], C[E];
+            for (; k < ncols; k++) column(ldg_stream(base + (long long)k * a.ldb), cs[k]);
+            float S[E], C[E];
 #pragma unroll
-        for (int e = 0; e < E / 2; e++) {
-            S[2 * e] = S2[e].x;
-            S[2 * e + 1] = S2[e].y;
-            C[2 * e] = C2[e].x;
-            C[2 * e + 1] = C2[e].y;
-        }
-        // epilogue
+            for (int e = 0; e < E / 2; e++) {
+                S[2 * e] = S2[e].x;
+                S[2 * e + 1] = S2[e].y;
+                C[2 * e] = C2[e].x;
+                C[2 * e + 1] = C2[e].y;
+            }
+            // epilogue
 #pragma unroll
-        for (int e = 0; e < E; e++) {
-            const long long i = row0 + e;
-            double acc;
-            if constexpr (ARITH == ARITH_DF32) {
-                if constexpr (EPI == EPI_SUB) {
-                    float wh, wl;
-                    if (a.wdf_in) {
-                        wh = a.wdf_in[i];
-                        wl = a.wdf_in[a.nrows + i];
+            for (int e = 0; e < E; e++) {
+                const long long i = row0 + e;
+                double acc;
+                if constexpr (ARITH == ARITH_DF32) {
+                    if constexpr (EPI == EPI_SUB) {
+                        float wh, wl;
+                        if (a.wdf_in) {
+                            wh = a.wdf_in[i];
+                            wl = a.wdf_in[a.nrows + i];
+                        } else {
+                            split_f64(a.w_in[i], wh, wl);
+                        }
+                        df_add(S[e], C[e], wh, wl);
+                    }
+                    if (M == 1 || (M == 0 && EPI == EPI_SUB && !a.w_out)) {
+                        // only the split copy is wanted (the first CGS pass when the second
+                        // always runs): the renormalised pair itself, no FP64 operation, no norms
+                        float h, l;
+                        two_sum(S[e], C[e], h, l);
+                        a.wdf_out[i] = h;
+                        a.wdf_out[a.nrows + i] = l;
+                        continue;
+                    }
+                    if constexpr (EPI == EPI_SUB) {
+                        // sum of squares in double-float on the FP32 pipe (GB300's FP64 pipe
+                        // runs at 1/64 of it): (h + l)^2 = h^2 + 2hl, h^2 exact as a pair
+                        float h, l;
+                        two_sum(S[e], C[e], h, l);
+                        if ((M == 2 || (M == 0 && a.counter)) && e < nvalid) {
+                            const float p = __fmul_rn(h, h);
+                            float q = __fmaf_rn(h, h, -p);
+                            q = __fmaf_rn(__fadd_rn(h, h), l, q);
+                            const float t = __fadd_rn(ssS, p), bb = __fsub_rn(t, ssS);
+                            ssC = __fadd_rn(ssC, __fadd_rn(__fadd_rn(__fsub_rn(ssS, __fsub_rn(t, bb)), __fsub_rn(p, bb)), q));
+                            ssS = t;
+                        }
+                        acc = df_to_double(h, l);
                     } else {
-                        split_f64(a.w_in[i], wh, wl);
+                        acc = df_to_double(S[e], C[e]);
                     }
-                    df_add(S[e], C[e], wh, wl);
-                }
-                if (EPI == EPI_SUB && !a.w_out) {
-                    // only the split copy is wanted (the first CGS pass when the second
-                    // always runs): the renormalised pair itself, no FP64 operation, no norms
-                    float h, l;
-                    two_sum(S[e], C[e], h, l);
-                    a.wdf_out[i] = h;
-                    a.wdf_out[a.nrows + i] = l;
-                    continue;
+                } else {
+                    acc = D[e];
+                    if constexpr (EPI == EPI_SUB) acc = __dadd_rn(a.w_in[i], acc);
                 }
                 if constexpr (EPI == EPI_SUB) {
-                    // sum of squares in double-float on the FP32 pipe (GB300's FP64 pipe
-                    // runs at 1/64 of it): (h + l)^2 = h^2 + 2hl, h^2 exact as a pair
-                    float h, l;
-                    two_sum(S[e], C[e], h, l);
-                    if (a.counter && i < a.n) {
-                        const float p = __fmul_rn(h, h);
-                        float q = __fmaf_rn(h, h, -p);
-                        q = __fmaf_rn(__fadd_rn(h, h), l, q);
-                        const float t = __fadd_rn(ssS, p), bb = __fsub_rn(t, ssS);
-                        ssC = __fadd_rn(ssC, __fadd_rn(__fadd_rn(__fsub_rn(ssS, __fsub_rn(t, bb)), __fsub_rn(p, bb)), q));
-                        ssS = t;
+                    a.w_out[i] = acc;
+                    if (M == 0 && a.wdf_out) {
+                        float h, l;
+                        split_f64(acc, h, l);
+                        a.wdf_out[i] = h;
+                        a.wdf_out[a.nrows + i] = l;
                     }
-                    acc = df_to_double(h, l);
+                    if ((M == 2 || (M == 0 && a.counter)) && e < nvalid) {   // the norms only when a last block reads them
+                        if constexpr (ARITH != ARITH_DF32) ss = __fma_rn(acc, acc, ss);
+                        const unsigned int ah = (unsigned int)__double2hiint(acc) & 0x7FFFFFFFu;
+                        const unsigned int al = (unsigned int)__double2loint(acc);
+                        if (ah > mxh || (ah == mxh && al > mxl)) {
+                            mxh = ah;
+                            mxl = al;
+                        }
+                    }
+                } else if constexpr (EPI == EPI_XUPD) {
+                    if (i < a.n) {
+                        double d = a.dinv ? __dmul_rn(a.dinv[i], acc) : acc;
+                        a.w_out[i] = __dadd_rn(a.w_out[i], d);
+                    }
                 } else {
-                    acc = df_to_double(S[e], C[e]);
+                    a.w_out[i] = acc;
                 }
-            } else {
-                acc = D[e];
-                if constexpr (EPI == EPI_SUB) acc = __dadd_rn(a.w_in[i], acc);
-            }
-            if constexpr (EPI == EPI_SUB) {
-                a.w_out[i] = acc;
-                if (a.wdf_out) {
-                    float h, l;
-                    split_f64(acc, h, l);
-                    a.wdf_out[i] = h;
-                    a.wdf_out[a.nrows + i] = l;
-                }
-                if (a.counter && i < a.n) {           // the norms only when a last block reads them
-                    if constexpr (ARITH != ARITH_DF32) ss = __fma_rn(acc, acc, ss);
-                    unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & 0x7FFFFFFFFFFFFFFFull;
-                    mxb = ab > mxb ? ab : mxb;
-                }
-            } else if constexpr (EPI == EPI_XUPD) {
-                if (i < a.n) {
-                    double d = a.dinv ? __dmul_rn(a.dinv[i], acc) : acc;
-                    a.w_out[i] = __dadd_rn(a.w_out[i], d);
-                }
-            } else {
-                a.w_out[i] = acc;
             }
         }
+    };
+    if constexpr (EPI == EPI_SUB && ARITH == ARITH_DF32) {
+        if (!a.w_out) segments(std::integral_constant<int, 1>{});
+        else if (!a.wdf_out && a.counter) segments(std::integral_constant<int, 2>{});
+        else segments(std::integral_constant<int, 0>{});
+    } else {
+        segments(std::integral_constant<int, 0>{});
     }
     if constexpr (EPI == EPI_SUB) {
         if (!a.counter) return;
         if constexpr (ARITH == ARITH_DF32) ss = df_to_double(ssS, ssC);
         ss = warp_sum(ss);
-        double mx = warp_max(__longlong_as_double((long long)mxb));
+        double mx = warp_max(__hiloint2double((int)mxh, (int)mxl));
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         if (lane == 0) { red_s[warp] = ss; red_m[warp] = mx; }
         __syncthreads();
@@ -990,68 +1015,79 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     if (xsplit) split_f64(xs, xsh, xsl);
     const float* vlo = dfrows ? a.valdf + a.nnz : nullptr;       // lo plane of the values
     float* ylo = dfrows ? a.ydf + a.ydf_ld : nullptr;            // lo plane of w
-    for (long long row = gid;; row += ngroups) {
-        const bool valid = row < a.n;
-        if constexpr (GROUP > 1) {
-            if (__all_sync(0xFFFFFFFFu, !valid)) break;   // warp-uniform exit around shuffles
-        } else {
-            if (!valid) break;
-        }
-        const int p0 = valid ? a.rowptr[row] : 0, p1 = valid ? a.rowptr[row + 1] : 0;
-        double s = 0.0;
-        if (dfrows) {
-            float S = 0.f, C = 0.f;
-            for (int p = p0 + lane_g; p < p1; p += GROUP) {
-                const float vh = a.valdf[p], vl = vlo[p];
-                const int cp = a.col[p];
-                if (!col_ok(cp, a.n, a.st)) continue;
-                float xh, xl;
-                xval_df<XFMT>(a.x, cp, xh, xl);
-                const float pr = __fmul_rn(vh, xh);
-                float er = __fmaf_rn(vh, xh, -pr);           // exact product error
-                er = __fmaf_rn(vl, xh, er);
-                if constexpr (!XEXACT) er = __fmaf_rn(vh, xl, er);
-                dfadd(S, C, pr, er);
-            }
+    // the row loop, compiled twice: once with the double-float products and once with
+    // FP64 FMAs, so neither path carries the other's instructions (predicated FP64-pipe
+    // instructions would still occupy GB300's narrow FP64 pipe)
+    auto rows = [&](auto df_tag) {
+        constexpr bool DF = decltype(df_tag)::value;
+        // 32-bit row arithmetic: CSR indices are int32, so n < 2^31 and row + ngroups
+        // stays below 2^32
+        const unsigned int n32 = (unsigned int)a.n, ng32 = (unsigned int)ngroups;
+        for (unsigned int row = (unsigned int)gid;; row += ng32) {
+            const bool valid = row < n32;
             if constexpr (GROUP > 1) {
+                if (__all_sync(0xFFFFFFFFu, !valid)) break;   // warp-uniform exit around shuffles
+            } else {
+                if (!valid) break;
+            }
+            const int p0 = valid ? a.rowptr[row] : 0, p1 = valid ? a.rowptr[row + 1] : 0;
+            double s = 0.0;
+            if constexpr (DF) {
+                float S = 0.f, C = 0.f;
+                for (int p = p0 + lane_g; p < p1; p += GROUP) {
+                    const float vh = a.valdf[p], vl = vlo[p];
+                    const int cp = a.col[p];
+                    if (!col_ok(cp, a.n, a.st)) continue;
+                    float xh, xl;
+                    xval_df<XFMT>(a.x, cp, xh, xl);
+                    const float pr = __fmul_rn(vh, xh);
+                    float er = __fmaf_rn(vh, xh, -pr);           // exact product error
+                    er = __fmaf_rn(vl, xh, er);
+                    if constexpr (!XEXACT) er = __fmaf_rn(vh, xl, er);
+                    dfadd(S, C, pr, er);
+                }
+                if constexpr (GROUP > 1) {
 #pragma unroll
-                for (int o = GROUP / 2; o > 0; o >>= 1) {
-                    const float S2 = __shfl_xor_sync(0xFFFFFFFFu, S, o), C2 = __shfl_xor_sync(0xFFFFFFFFu, C, o);
-                    const float t = __fadd_rn(S, S2), bb = __fsub_rn(t, S);
-                    C = __fadd_rn(__fadd_rn(C, C2), __fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(S2, bb)));
-                    S = t;
+                    for (int o = GROUP / 2; o > 0; o >>= 1) {
+                        const float S2 = __shfl_xor_sync(0xFFFFFFFFu, S, o), C2 = __shfl_xor_sync(0xFFFFFFFFu, C, o);
+                        const float t = __fadd_rn(S, S2), bb = __fsub_rn(t, S);
+                        C = __fadd_rn(__fadd_rn(C, C2), __fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(S2, bb)));
+                        S = t;
+                    }
+                }
+                if (valid && lane_g == 0) {
+                    float hi, lo;
+                    two_sum(S, C, hi, lo);                       // renormalise
+                    if (xsplit) {                                // integer / power-of-two scales
+                        const float p = __fmul_rn(hi, xsh);
+                        float e = __fmaf_rn(hi, xsh, -p);
+                        e = __fmaf_rn(hi, xsl, e);
+                        e = __fmaf_rn(lo, xsh, e);
+                        two_sum(p, e, hi, lo);
+                    }
+                    a.ydf[row] = hi;
+                    ylo[row] = lo;
+                    const float p = __fmul_rn(hi, hi);           // ||y||^2 in double-float
+                    float e = __fmaf_rn(hi, hi, -p);
+                    e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
+                    dfadd(ssS, ssC, p, e);
+                }
+                continue;
+            } else {
+                for (int p = p0 + lane_g; p < p1; p += GROUP) {
+                    const int cp = a.col[p];
+                    if (col_ok(cp, a.n, a.st)) s = __fma_rn(a.val[p], xval(cp), s);
+                }
+                if constexpr (GROUP > 1) {
+#pragma unroll
+                    for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
                 }
             }
-            if (valid && lane_g == 0) {
-                float hi, lo;
-                two_sum(S, C, hi, lo);                       // renormalise
-                if (xsplit) {                                // integer / power-of-two scales
-                    const float p = __fmul_rn(hi, xsh);
-                    float e = __fmaf_rn(hi, xsh, -p);
-                    e = __fmaf_rn(hi, xsl, e);
-                    e = __fmaf_rn(lo, xsh, e);
-                    two_sum(p, e, hi, lo);
-                }
-                a.ydf[row] = hi;
-                ylo[row] = lo;
-                const float p = __fmul_rn(hi, hi);           // ||y||^2 in double-float
-                float e = __fmaf_rn(hi, hi, -p);
-                e = __fmaf_rn(__fadd_rn(hi, hi), lo, e);
-                dfadd(ssS, ssC, p, e);
-            }
-            continue;
-        } else {
-            for (int p = p0 + lane_g; p < p1; p += GROUP) {
-                const int cp = a.col[p];
-                if (col_ok(cp, a.n, a.st)) s = __fma_rn(a.val[p], xval(cp), s);
-            }
-            if constexpr (GROUP > 1) {
-#pragma unroll
-                for (int o = GROUP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-            }
+            if (valid && lane_g == 0) finish(row, s);
         }
-        if (valid && lane_g == 0) finish(row, s);
-    }
+    };
+    if (dfrows) rows(std::true_type{});
+    else rows(std::false_type{});
     const double mx = __longlong_as_double((long long)mxb);
     if constexpr (MODE == SPMV_PLAIN || MODE == SPMV_ACCUM) return;
     else {

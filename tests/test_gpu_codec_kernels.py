@@ -129,3 +129,21 @@ def test_basis_dot_and_axpy_parity(fmt, arith, n, ncols):
     rel = 1.2e-16 * (ncols + 2) if arith == "fp64" else 2.0 ** -45 * (ncols + 2)
     assert np.all(np.abs(got[:n] - ref) <= rel * scale_ref + 1e-300)
     assert np.all(got[n:] == 0.0)
+
+
+def test_decode_f32_special_values():
+    """The integer FP32 -> FP64 widening of the decoders: zeros, subnormals (every leading
+    bit position), the normal range ends, infinities and NaN, against numpy's exact
+    conversion (scale 1: the decode is the widening itself)."""
+    torch, cb = need_gpu()
+    bits = [0x00000000, 0x80000000, 0x7F7FFFFF, 0xFF7FFFFF, 0x00800000, 0x80800000, 0x3F800000,
+            0x7F800000, 0xFF800000, 0x7FC00000]
+    bits += [1 << k for k in range(23)] + [0x80000000 | ((1 << k) | 1) for k in range(1, 23)]
+    bits += [0x007FFFFF, 0x807FFFFF, 0x00400001, 0x00000003]
+    b = np.array(bits, dtype=np.uint32)
+    ref = b.view(np.float32).astype(np.float64)
+    ct = torch.from_numpy(b.view(np.int32)).cuda()
+    got = cb.decode("f32", ct, 1.0).cpu().numpy()
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
