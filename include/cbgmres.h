@@ -90,8 +90,10 @@ typedef enum { CBG_ORTHO_CGS = 0, CBG_ORTHO_MGS = 1 } cbg_ortho;
  *   basis at HBM speed.
  * CBG_ARITH_FP64: every product and sum is a native FP64 operation, as the paper
  *   prescribes; on GB300 the basis products then run at FP64-pipe speed.
- * The residual SpMV (b - Ax, the convergence judge), norms, Givens rotations, the
- * least-squares solve and the solution update are FP64 in both modes. */
+ * With CBG_ARITH_DF32 the norms of the Arnoldi step (omega = ||A v_j|| in the SpMV,
+ * ||w|| in the last CGS pass) are also summed in double-float per thread and combined
+ * in FP64.  The residual SpMV (b - Ax, the convergence judge), ||r||, the Givens
+ * rotations, the least-squares solve and the solution update are FP64 in both modes. */
 typedef enum { CBG_ARITH_DF32 = 0, CBG_ARITH_FP64 = 1 } cbg_arith;
 
 /* status codes */

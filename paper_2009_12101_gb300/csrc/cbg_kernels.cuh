@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
                     }
                     if constexpr (EPI == EPI_SUB) {
                         // sum of squares in double-float on the FP32 pipe (GB300's FP64 pipe
-                        // runs at 1/64 of it): (h + l)^2 = h^2 + 2hl, h^2 exact as a pair
+                        // runs at about 1/70 of it): (h + l)^2 = h^2 + 2hl, h^2 exact as a pair
                         float h, l;
                         two_sum(S[e], C[e], h, l);
                         if ((M == 2 || (M == 0 && a.counter)) && e < nvalid) {
