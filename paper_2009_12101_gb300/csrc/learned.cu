@@ -111,12 +111,37 @@ __global__ void k_pair_accumulate(const int* rowptr, const int* col, const signe
     }
 }
 
-__global__ void k_grad_reduce(const float* gpart, int nblk, double* grad)
+// grad[idx] = sum over the CTAs' partials gpart[b][idx] in FP64.  Block x covers the 32
+// parameters 32x .. 32x+31 (one per lane, coalesced rows of gpart); its eight warps take
+// the partials b = w, w + 8, ... (eight loads in flight per lane), and the warps' sums are
+// added in warp order: a fixed order for a given nblk.
+constexpr int GR_THREADS = 256;
+__global__ void __launch_bounds__(GR_THREADS) k_grad_reduce(const float* gpart, int nblk, double* grad)
 {
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NPARAM; idx += gridDim.x * blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nblk; b++) t += (double)gpart[(long long)b * NPARAM + idx];
-        grad[idx] = t;
+    __shared__ double part[GR_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int idx = blockIdx.x * 32 + lane;
+    double t = 0.0;
+    if (idx < NPARAM) {
+        for (int b0 = warp; b0 < nblk; b0 += 8 * (GR_THREADS / 32)) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int b = b0 + u * (GR_THREADS / 32);
+                v[u] = b < nblk ? gpart[(long long)b * NPARAM + idx] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (b0 + u * (GR_THREADS / 32) < nblk) t = __dadd_rn(t, f32_to_f64_exact(v[u]));
+        }
+    }
+    part[warp][lane] = t;
+    __syncthreads();
+    if (warp == 0 && idx < NPARAM) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < GR_THREADS / 32; w++) s = __dadd_rn(s, part[w][lane]);
+        grad[idx] = s;
     }
 }
 
@@ -355,7 +380,7 @@ int cbg_spai_train(cbg_spai* s, int steps, double lr, double* loss_first, double
         // the loss is read back once, before the first update (no per-step synchronisation)
         int rc = train_pass(s, it == 0 ? &l0 : nullptr);
         if (rc) return rc;
-        k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->gpart, s->tc_grid, s->grad);
+        k_grad_reduce<<<(NPARAM + 31) / 32, GR_THREADS, 0, s->stream>>>(s->gpart, s->tc_grid, s->grad);
         s->step++;
         k_adam<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->master, s->bf, s->grad, s->m1, s->m2, s->step,
                                                             (float)lr, 0.9f, 0.999f, 1e-8f);
@@ -465,7 +490,7 @@ int cbg_mlp_backward(int64_t rows, const float* feat, const float* params_host, 
         a.fault = fault;
         rc = check(mlp_tc_launch(MLP_BWD, grid, st, a));
         if (!rc) {
-            k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(gp, grid, g);
+            k_grad_reduce<<<(NPARAM + 31) / 32, GR_THREADS, 0, st>>>(gp, grid, g);
             rc = check(cudaGetLastError());
         }
         int hf = 0;

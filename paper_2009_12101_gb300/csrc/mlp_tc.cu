@@ -371,7 +371,9 @@ __global__ void __launch_bounds__(MT, 1) k_mlp_tc(MlpArgs a)
             const float dd = reinterpret_cast<const float*>(sm + S_D)[t];
             const double dg = reinterpret_cast<const double*>(sm + S_DIAG)[t];
             const unsigned int mk = sm[S_MASK + t];
-            const float id = valid ? (float)(1.0 / dg) : 0.f;
+            // 1 / a_ii in FP32 (an FP64 division per row would sit on GB300's narrow FP64 pipe
+            // between two block barriers)
+            const float id = valid ? __frcp_rn(f64_to_f32_rn(dg)) : 0.f;
             float p[7];
 #pragma unroll
             for (int k = 0; k < 7; k++) p[k] = (mk >> k) & 1u ? y[k] * id : 0.f;
