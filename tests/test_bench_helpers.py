@@ -1,0 +1,37 @@
+"""Host logic of bench.py (no GPU): the roofline's traffic figures come from the committed
+ncu summary, the batch split covers every system once, and the profiling-cases module
+imports without a device."""
+import importlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def test_traffic_per_element_read_from_the_profile_summary():
+    import bench
+    t = bench.ncu_traffic_per_element("f32")
+    assert set(t) == {"basis_dot", "basis_axpy"}
+    # a launch reads every code once plus w's planes: a little above 4 bytes per element
+    for v in t.values():
+        assert 4.0 < v < 4.5
+    assert bench.ncu_traffic_per_element("e4m3") == {}
+
+
+def test_shard_units_cover_every_unit_once():
+    import bench
+    for n in (0, 1, 7, 512):
+        for world in (1, 2, 3, 8):
+            shares = [list(bench.shard_units(n, world, r)) for r in range(world)]
+            flat = [i for s in shares for i in s]
+            assert flat == list(range(n))                       # contiguous, in rank order
+            sizes = [len(s) for s in shares]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def test_profile_cases_module_imports_without_a_gpu():
+    pc = importlib.import_module("paper_2009_12101_gb300.profile_cases")
+    for name in ("case_gemv", "case_spmv", "case_mlp", "main"):
+        assert callable(getattr(pc, name))
