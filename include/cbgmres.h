@@ -131,10 +131,11 @@ typedef struct {
                               * (DF32 arithmetic; padding <= nnz/4, else              *
                               * CBG_ERR_UNSUPPORTED).  Automatic times 1, 2, .., 32    *
                               * lanes and the sliced-ELL copy at create on matrices   *
-                              * of >= 65536 rows (shortest of 5 launches each) and    *
-                              * keeps the fastest, the copy only when 3 % faster than *
-                              * every CSR schedule (else it is freed); below 65536    *
-                              * rows it picks by nonzeros per row                     */
+                              * of >= 65536 rows (shortest of 5 launches each, L2    *
+                              * flushed before each) and keeps the fastest, the copy  *
+                              * only when 10 % faster than every CSR schedule (else   *
+                              * it is freed); below 65536 rows it picks by nonzeros   *
+                              * per row                                               */
     double eta;              /* conditional re-orthogonalisation threshold (1/sqrt 2)  */
     double breakdown_eps;    /* breakdown when !(h_{j+1,j} > eps * omega) (2^-46)      */
     void* stream;            /* cudaStream_t for all work (NULL: default stream)        */
