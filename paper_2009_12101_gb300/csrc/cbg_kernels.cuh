@@ -788,18 +788,34 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     const double hs = a.hexp ? pow2d(a.hexp) : 1.0;
     hn = __dmul_rn(hn, hs);
     const double omega = __dmul_rn(omega_raw, hs);
-#pragma unroll 4
-    for (int i = lane; i <= j + 1; i += 32) {
-        double hv = 0.0;
-        if (i <= j) {
-            hv = __ldcg(a.d.h + i);
-            if (reorth) hv = __dadd_rn(hv, __ldcg(a.d.u + i));
-            hv = __dmul_rn(hv, hs);
-        } else {
-            hv = hn;
+    // up to 128 entries per round: all of a round's loads are issued before the first of
+    // them is used (issued one entry at a time, every entry cost an L2 round trip)
+    for (int base = lane; base <= j + 1; base += 128) {
+        double hv[4], uv[4], cv[4], sv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = base + 32 * q;
+            hv[q] = i <= j ? __ldcg(a.d.h + i) : 0.0;
+            uv[q] = i <= j ? __ldcg(a.d.u + i) : 0.0;   // read always, added only after pass 2
+            cv[q] = i < j ? a.d.cs[i] : 0.0;
+            sv[q] = i < j ? a.d.sn[i] : 0.0;
         }
-        sR[i] = hv;
-        if (i < j) { scs[i] = a.d.cs[i]; ssn[i] = a.d.sn[i]; }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = base + 32 * q;
+            if (i > j + 1) break;
+            double v = hn;
+            if (i <= j) {
+                v = hv[q];
+                if (reorth) v = __dadd_rn(v, uv[q]);
+                v = __dmul_rn(v, hs);
+            }
+            sR[i] = v;
+            if (i < j) {
+                scs[i] = cv[q];
+                ssn[i] = sv[q];
+            }
+        }
     }
     __syncwarp();
     double* Hc = a.d.H + (long long)j * ldh;
