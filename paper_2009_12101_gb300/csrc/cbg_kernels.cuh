@@ -784,10 +784,9 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
     const int kcap = st->kcap, record = st->record;
     const long long iters = st->iters, reorths = st->reorths, hist_cap = st->hist_cap;
     const double gj = a.d.g[j];
-    // back from the power-of-two normalised operator (exact)
+    // back from the power-of-two normalised operator (exact); hn and omega are scaled
+    // after the staging loads are issued, so that those do not wait for the state loads
     const double hs = a.hexp ? pow2d(a.hexp) : 1.0;
-    hn = __dmul_rn(hn, hs);
-    const double omega = __dmul_rn(omega_raw, hs);
     // up to 128 entries per round: all of a round's loads are issued before the first of
     // them is used (issued one entry at a time, every entry cost an L2 round trip)
     for (int base = lane; base <= j + 1; base += 128) {
@@ -804,7 +803,7 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         for (int q = 0; q < 4; q++) {
             const int i = base + 32 * q;
             if (i > j + 1) break;
-            double v = hn;
+            double v = __dmul_rn(hn, hs);
             if (i <= j) {
                 v = hv[q];
                 if (reorth) v = __dadd_rn(v, uv[q]);
@@ -818,6 +817,8 @@ static __device__ void arnoldi_finalize(const StoreArgs& a, double hn, double* s
         }
     }
     __syncwarp();
+    hn = __dmul_rn(hn, hs);
+    const double omega = __dmul_rn(omega_raw, hs);
     double* Hc = a.d.H + (long long)j * ldh;
     for (int i = lane; i < ldh; i += 32) Hc[i] = i <= j + 1 ? sR[i] : 0.0;   // raw column
     __syncwarp();
