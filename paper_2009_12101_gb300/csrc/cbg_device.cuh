@@ -439,4 +439,54 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// maximum of non-negative doubles over the warp, compared as bit patterns with 32-bit
+// integer operations (no FP64 instruction: GB300's FP64 pipe is narrow and slow)
+__device__ __forceinline__ double warp_max_nonneg(double v)
+{
+    unsigned int hi = (unsigned int)__double2hiint(v), lo = (unsigned int)__double2loint(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned int h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o), l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        if (h2 > hi || (h2 == hi && l2 > lo)) {
+            hi = h2;
+            lo = l2;
+        }
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// The block's sum of the threads' ss and maximum of their mx (mx >= 0): a shuffle tree in
+// every warp, then warp 0 folds the warps' results with a second tree (five dependent
+// FP64 additions instead of one per warp).  red_s, red_m: shared, blockDim.x / 32 entries.
+// All threads call it; the totals are valid in warp 0.
+__device__ __forceinline__ void block_sum_max(double ss, double mx, double* red_s, double* red_m, double& s,
+                                              double& m)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    ss = warp_sum(ss);
+    mx = warp_max_nonneg(mx);
+    if (lane == 0) {
+        red_s[warp] = ss;
+        red_m[warp] = mx;
+    }
+    __syncthreads();
+    s = 0.0;
+    m = 0.0;
+    if (warp == 0) {                 // a tree over the first pow2 >= nw lanes only
+        s = lane < nw ? red_s[lane] : 0.0;
+        m = lane < nw ? red_m[lane] : 0.0;
+        unsigned int hi = (unsigned int)__double2hiint(m), lo = (unsigned int)__double2loint(m);
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o >= nw) continue;   // lanes >= nw hold zeros: nothing to fold from there
+            s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            const unsigned int h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o), l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+            if (h2 > hi || (h2 == hi && l2 > lo)) {
+                hi = h2;
+                lo = l2;
+            }
+        }
+        m = __hiloint2double((int)hi, (int)lo);
+    }
+}
+
 }  // namespace cbg

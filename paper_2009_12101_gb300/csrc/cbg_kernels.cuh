@@ -105,16 +105,17 @@ __device__ __forceinline__ bool last_block(unsigned int* counter)
 }
 
 // The last block's sum of squares and maximum over the per-block pairs (part[2b],
-// part[2b+1]), b < np, computed by every thread of the block (all threads must call it):
-// thread t adds the pairs t, t + blockDim.x, ... in that order, the warps fold their lanes
-// with a fixed shuffle tree and every thread adds the warps' results in warp order, so the
-// result depends only on np and blockDim.x.  The loads of two pairs are issued before
-// they are added: the chain is about np / (2 blockDim.x) memory round trips long.
+// part[2b+1]), b < np (all threads must call it; the results are valid in warp 0):
+// thread t adds the pairs t, t + blockDim.x, ... in that order, then block_sum_max folds
+// the threads with fixed shuffle trees, so the result depends only on np and
+// blockDim.x.  The loads of two pairs are issued before they are added; the maxima of
+// the non-negative values are taken on their bit patterns (integer operations).
 __device__ __forceinline__ void block_reduce_norm_parts(const double* part, int np, double& ss, double& mx)
 {
     __shared__ double rs[32], rm[32];
     const int nt = blockDim.x;
-    double s = 0.0, m = 0.0;
+    double s = 0.0;
+    unsigned int mh = 0u, ml = 0u;
     for (int p0 = threadIdx.x; p0 < np; p0 += 2 * nt) {
         double vs[2], vm[2];
 #pragma unroll
@@ -127,23 +128,14 @@ __device__ __forceinline__ void block_reduce_norm_parts(const double* part, int 
         for (int u = 0; u < 2; u++)
             if (p0 + u * nt < np) {
                 s += vs[u];
-                m = fmax(m, vm[u]);
+                const unsigned int h = (unsigned int)__double2hiint(vm[u]), l = (unsigned int)__double2loint(vm[u]);
+                if (h > mh || (h == mh && l > ml)) {
+                    mh = h;
+                    ml = l;
+                }
             }
     }
-    s = warp_sum(s);
-    m = warp_max(m);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        rs[warp] = s;
-        rm[warp] = m;
-    }
-    __syncthreads();
-    ss = 0.0;
-    mx = 0.0;
-    for (int w = 0; w < (nt >> 5); w++) {
-        ss += rs[w];
-        mx = fmax(mx, rm[w]);
-    }
+    block_sum_max(s, __hiloint2double((int)mh, (int)ml), rs, rm, ss, mx);
 }
 
 // The last block's sums over the per-block partials of nitems items: item i is
@@ -708,14 +700,9 @@ __global__ void __launch_bounds__(THREADS, FmtInfo<FMT>::bytes >= 8 ? 4 : (FmtIn
     if constexpr (EPI == EPI_SUB) {
         if (!a.counter) return;
         if constexpr (ARITH == ARITH_DF32) ss = df_to_double(ssS, ssC);
-        ss = warp_sum(ss);
-        double mx = warp_max(__hiloint2double((int)mxh, (int)mxl));
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mx; }
-        __syncthreads();
+        double s, m;
+        block_sum_max(ss, __hiloint2double((int)mxh, (int)mxl), red_s, red_m, s, m);
         if (threadIdx.x == 0) {
-            double s = 0.0, m = 0.0;
-            for (int w = 0; w < THREADS / 32; w++) { s += red_s[w]; m = fmax(m, red_m[w]); }
             a.part_norm[2 * blockIdx.x] = s;
             a.part_norm[2 * blockIdx.x + 1] = m;
         }
@@ -1109,14 +1096,9 @@ __global__ void __launch_bounds__(THREADS) k_spmv(SpmvArgs a)
     if constexpr (MODE == SPMV_PLAIN || MODE == SPMV_ACCUM) return;
     else {
         if (dfrows) ss = df_to_double(ssS, ssC);
-        ss = warp_sum(ss);
-        const double mxw = warp_max(mx);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red_s[warp] = ss; red_m[warp] = mxw; }
-        __syncthreads();
+        double s, m;
+        block_sum_max(ss, mx, red_s, red_m, s, m);
         if (threadIdx.x == 0) {
-            double s = 0.0, m = 0.0;
-            for (int w = 0; w < THREADS / 32; w++) { s += red_s[w]; m = fmax(m, red_m[w]); }
             a.part[2 * blockIdx.x] = s;
             a.part[2 * blockIdx.x + 1] = m;
         }
@@ -1169,7 +1151,7 @@ template <int XFMT>
 __global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
 {
     if (a.active && *a.active == 0) return;
-    __shared__ double red_s[THREADS / 32];
+    __shared__ double red_s[THREADS / 32], red_m[THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool XEXACT = XFMT == F32 || XFMT == F16 || XFMT == BF16 || XFMT == E4M3 || XFMT == I16;
     const double xs = a.xscale_dev ? *a.xscale_dev : 1.0;
@@ -1241,12 +1223,9 @@ __global__ void __launch_bounds__(THREADS) k_spmv_sell(SellArgs a)
             dfadd(ssS, ssC, p, e);
         }
     }
-    double ss = warp_sum(df_to_double(ssS, ssC));
-    if (lane == 0) red_s[warp] = ss;
-    __syncthreads();
+    double t, tm;
+    block_sum_max(df_to_double(ssS, ssC), 0.0, red_s, red_m, t, tm);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < THREADS / 32; w++) t += red_s[w];
         a.part[2 * blockIdx.x] = t;
         a.part[2 * blockIdx.x + 1] = 0.0;
     }

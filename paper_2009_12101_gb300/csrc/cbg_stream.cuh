@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
     for (int col = threadIdx.x; col < ncols; col += DOT_THREADS) a.part[(long long)blockIdx.x * MAXCOLS + col] = red_tot[col];
     // Grid barrier (the kernel is launched cooperatively: every block is resident), then
     // block b adds the partials of the columns b, b + gridDim.x, ...: one load per thread
-    // and column, one warp shuffle tree per warp, the warps' sums in warp order.  The
+    // and column, one warp shuffle tree per warp, then one over the warps' sums.  The
     // cross-block sum is spread over all SMs instead of one last block, whose FP64 pipe
     // (a few FP64 operations per clock per SM on GB300) and serial L2 round trips would
     // otherwise add tens of microseconds to a launch.
@@ -337,13 +337,18 @@ __global__ void __launch_bounds__(DOT_THREADS, 1) k_basis_dot_tma(DotArgs a, int
 #pragma unroll
             for (int k = 0; k < 4; k++) wsum_sh[warp][k] = v[k];
         __syncthreads();
-        if (threadIdx.x < 4) {
-            const int col = c0 + threadIdx.x * nb;
-            if (col < ncols) {
-                double sum = 0.0;
-                for (int w = 0; w < DOT_CW + 1; w++) sum += wsum_sh[w][threadIdx.x];
-                a.out[col] = sum * a.scales[col];
-            }
+        if (warp == 0) {
+            // the 17 warps' sums of the four columns at once: lane l takes column l / 8 and
+            // warps l % 8, l % 8 + 8, l % 8 + 16 (in that order), then a three-level tree
+            // within each group of eight lanes
+            const int k = lane >> 3, w0 = lane & 7;
+            double sum = 0.0;
+#pragma unroll
+            for (int w = w0; w < DOT_CW + 1; w += 8) sum += wsum_sh[w][k];
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            const int col = c0 + k * nb;
+            if (w0 == 0 && col < ncols) a.out[col] = sum * a.scales[col];
         }
         __syncthreads();
     }
