@@ -26,6 +26,9 @@ template <int FMT> struct Launcher {
                        double* out);
     static int occupancy_dot();
     static int occupancy_axpy();
+    // resident blocks per SM of the per-step SpMV kernels of this code format (the CSR
+    // Arnoldi kernel with one and 32 lanes per row, and the sliced-ELL kernel): the least
+    static int occupancy_spmv();
     // batched persistent solve with thread-block clusters of `cluster` blocks
     static cudaError_t batched(int cluster, int grid, size_t smem, cudaStream_t s, const BatchArgs& a);
     static int batched_max_clusters(int cluster, size_t smem);

@@ -124,6 +124,15 @@ template <int FMT> int Launcher<FMT>::occupancy_axpy()
     return b;
 }
 
+template <int FMT> int Launcher<FMT>::occupancy_spmv()
+{
+    int b1 = 0, b32 = 0, bs = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_spmv<FMT, 1, SPMV_ARNOLDI>, THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_spmv<FMT, 32, SPMV_ARNOLDI>, THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_spmv_sell<FMT>, THREADS, 0);
+    return std::min(b1, std::min(b32, bs));
+}
+
 }  // namespace cbg
 
 namespace cbg {

@@ -86,6 +86,7 @@ struct Ops {
     void (*decode)(int, cudaStream_t, const unsigned char*, long long, double, double*);
     int (*occ_dot)();
     int (*occ_axpy)();
+    int (*occ_spmv)();
 };
 
 template <int F> Ops make_ops()
@@ -93,7 +94,7 @@ template <int F> Ops make_ops()
     return Ops{&Launcher<F>::dot, &Launcher<F>::axpy, &Launcher<F>::dot_tma,
                &Launcher<F>::tma_fits, &Launcher<F>::store, &Launcher<F>::spmv_code, &Launcher<F>::spmv_sell,
                &Launcher<F>::encode, &Launcher<F>::decode, &Launcher<F>::occupancy_dot,
-               &Launcher<F>::occupancy_axpy};
+               &Launcher<F>::occupancy_axpy, &Launcher<F>::occupancy_spmv};
 }
 
 const Ops& ops_for(int fmt)
@@ -1281,7 +1282,12 @@ int cbgmres_create(const cbg_csr* A, int restart, int fmt, const cbg_options* op
     // launch geometry (format-dependent parts: set_format; with options.adapt the
     // per-block partial arrays are sized for every format of the ladder)
     const int sms = num_sms();
-    const int occ_spmv = std::max(1, spmv_occupancy());
+    // one grid for every SpMV of the handle: the least occupancy of the FP64-vector kernels
+    // and of the per-step kernels of every format the handle may use, so that no SpMV
+    // launch spills into a partial second wave
+    int occ_min = spmv_occupancy();
+    for (int f = fmt; f >= 0; f = o.adapt ? promote_format(f) : -1) occ_min = std::min(occ_min, ops_for(f).occ_spmv());
+    const int occ_spmv = std::max(1, occ_min);
     h->fmt0 = fmt;
     h->grid_store = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 4);
     h->group = o.spmv_group > 0 ? o.spmv_group : pick_group(n, nnz);
