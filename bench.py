@@ -316,6 +316,21 @@ def roofline_from_profile(prof: dict, fmt: str, kernel_names: dict, peak: float,
             "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms}
 
 
+def kernel_class_table(prof: dict) -> dict:
+    """Per kernel class of a profiled solve: share of the summed CUDA-event time, launches,
+    average microseconds per launch and algorithmic GB/s (the library's byte model)."""
+    total = sum(p["ms"] for p in prof.values())
+    out = {}
+    for c, p in prof.items():
+        if p["launches"] <= 0:
+            continue
+        out[c] = {"share": round(p["ms"] / total, 4) if total > 0 else None,
+                  "launches": int(p["launches"]),
+                  "us_per_launch": round(1e3 * p["ms"] / p["launches"], 2),
+                  "gbs": round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) if p["ms"] > 0 and p["bytes"] > 0 else None}
+    return out
+
+
 def e2e_host_ratio(solvers: dict, base: str, head: str, b: np.ndarray, n: int, tol: float, maxit: int, reps: int):
     """Same metric end to end through cbgmres_solve_host (pinned host b and x, the copies
     inside the timed region): time(base) / time(head)."""
@@ -1046,7 +1061,8 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
-                "basis_gemv_gbs_by_format": gemv}
+                "basis_gemv_gbs_by_format": gemv,
+                "kernel_classes": kernel_class_table(ph)}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None

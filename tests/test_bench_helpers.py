@@ -35,3 +35,15 @@ def test_profile_cases_module_imports_without_a_gpu():
     pc = importlib.import_module("paper_2009_12101_gb300.profile_cases")
     for name in ("case_gemv", "case_spmv", "case_mlp", "main"):
         assert callable(getattr(pc, name))
+
+
+def test_kernel_class_table_shares_and_rates():
+    import bench
+    prof = {"basis_dot": {"ms": 30.0, "bytes": 1.5e11, "launches": 1000},
+            "spmv": {"ms": 10.0, "bytes": 4.0e10, "launches": 500},
+            "store": {"ms": 0.0, "bytes": 0.0, "launches": 0}}
+    t = bench.kernel_class_table(prof)
+    assert set(t) == {"basis_dot", "spmv"}                     # classes never launched left out
+    assert abs(t["basis_dot"]["share"] - 0.75) < 1e-12
+    assert t["spmv"]["us_per_launch"] == 20.0
+    assert t["basis_dot"]["gbs"] == 5000.0 and t["spmv"]["gbs"] == 4000.0
