@@ -26,6 +26,9 @@ _SRC = os.path.join(_HERE, "cbg_oracle.c")
 _HDR = os.path.join(_HERE, "cbg_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+# A prebuilt copy of the oracle to load instead of building this one: the planted-mistake
+# tests (tests/test_oracle_mutants.py) point it at copies with one deliberate error each.
+_LIB_OVERRIDE = os.environ.get("CBG_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -84,7 +87,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(_LIB_OVERRIDE or build())
             vp, i64, d = C.c_void_p, C.c_int64, C.c_double
             for name in ("or_vec_f64_to_f16", "or_vec_f16_to_f64", "or_vec_f32_to_bf16",
                          "or_vec_bf16_to_f64", "or_vec_f32_to_e4m3", "or_vec_e4m3_to_f64"):

@@ -175,6 +175,25 @@ def test_orthogonality_f64_cgs2(oracle_lib):
     assert np.linalg.norm(np.eye(V.shape[1]) - V.T @ V, 2) <= 1e-13
 
 
+@pytest.mark.parametrize("delta", [1e-8, 1e-10, 1e-12])
+def test_orthogonality_cgs2_near_invariant_krylov_space(oracle_lib, delta):
+    """A = I + delta E (E Gaussian): each new direction A v_j - V h is about delta of
+    omega = ||A v_j||, so after the first CGS pass w still carries components along V of
+    the order of the rounding of omega -- for small delta comparable to w itself.  The
+    second pass removes them (CGS2, "twice is enough"), and v_{j+1} = w / h_{j+1,j} is a
+    unit vector only if h_{j+1,j} is the norm after that pass (Fig. 1): the basis stays
+    orthonormal to working precision."""
+    n = 12
+    rng = np.random.default_rng(11)
+    M = np.eye(n) + delta * rng.standard_normal((n, n))
+    A = W.from_dense(M)
+    b = rng.standard_normal(n)
+    r = O.gmres(A, b, m=6, tol=0.0, maxit=6, want_V1=True)
+    V = r["V1"]
+    assert V.shape[1] == 7
+    assert np.linalg.norm(np.eye(7) - V.T @ V, 2) <= 1e-14
+
+
 @pytest.mark.parametrize("fmt,bound", [("f32", 1e-6), ("i32", 1e-8), ("f16", 5e-3), ("i16", 5e-4)])
 def test_orthogonality_compressed(oracle_lib, fmt, bound):
     A = W.convdiff3d(8)
