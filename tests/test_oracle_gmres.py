@@ -249,6 +249,40 @@ def test_reorth_modes(oracle_lib):
     assert rn["reorths"] == 0
 
 
+def test_conditional_reorth_limits(oracle_lib):
+    """Fig. 1 re-orthogonalises when h_{j+1,j} < eta omega: with eta = 0 the test never
+    holds (the conditional solve is the one that never re-orthogonalises, bit for bit),
+    with eta beyond any ratio it always holds (the solve that always does)."""
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    kw = dict(m=30, tol=1e-10, maxit=3000)
+    ra = O.gmres(A, b, reorth=O.REORTH_ALWAYS, **kw)
+    rn = O.gmres(A, b, reorth=O.REORTH_NEVER, **kw)
+    r0 = O.gmres(A, b, reorth=O.REORTH_CONDITIONAL, eta=0.0, **kw)
+    rinf = O.gmres(A, b, reorth=O.REORTH_CONDITIONAL, eta=1e300, **kw)
+    assert r0["reorths"] == 0 and r0["iters"] == rn["iters"] and np.array_equal(r0["x"], rn["x"])
+    assert rinf["reorths"] == rinf["iters"] == ra["iters"] and np.array_equal(rinf["x"], ra["x"])
+
+
+@pytest.mark.parametrize("k", [-60, 40])
+def test_power_of_two_operator_scaling_is_exact(oracle_lib, k):
+    """GMRES commutes with scaling A by 2^k: every product, norm and coefficient scales
+    exactly in binary floating point, the Givens rotations and the tests of Fig. 1
+    (h_{j+1,j} against eta omega, the breakdown test against omega) are ratios, so the
+    solve of (2^k A) x = b returns 2^-k times the x of A x = b, bit for bit, after the same
+    steps."""
+    A = W.convdiff3d(8)
+    b = W.rhs_sin(A.n)
+    As = W.CSR(A.n, A.rowptr, A.col, A.val * 2.0 ** k)
+    for fmt in (O.F64, O.F32, O.I16):
+        r = O.gmres(A, b, m=20, fmt=fmt, tol=1e-10, maxit=3000, hist_cap=3000)
+        rs = O.gmres(As, b, m=20, fmt=fmt, tol=1e-10, maxit=3000, hist_cap=3000)
+        assert r["status"] == rs["status"] == O.OK
+        assert r["iters"] == rs["iters"] and r["cycles"] == rs["cycles"]
+        assert np.array_equal(rs["x"] * 2.0 ** k, r["x"])
+        assert np.array_equal(rs["hist"], r["hist"])
+
+
 def test_literal_fig1_clause_truncates_cycles(oracle_lib):
     """Reading R2: the printed second clause of Fig. 1's breakdown test ends a cycle as soon as
     h_{j+1,j} < eta * omega; on this problem that happens within the first steps."""

@@ -1,7 +1,8 @@
 """Pins for the oracle's learned-preconditioner pieces (no counterpart in the paper, so
-parity is pinned to mathematics): the MLP backward against central finite differences
-of its forward, and the per-row statistics formulation of the loss against the loss
-evaluated directly on explicit (r, e) pairs with an explicit sparse P."""
+parity is pinned to mathematics): the MLP forward on weight sets whose network is a
+known function, the backward against central finite differences of the forward, and the
+per-row statistics formulation of the loss against the loss evaluated directly on
+explicit (r, e) pairs with an explicit sparse P."""
 import numpy as np
 import scipy.sparse as sp
 
@@ -31,6 +32,33 @@ def test_mlp_backward_matches_finite_differences(oracle_lib):
         e = np.zeros_like(p); e[i] = h
         fd = (f(p + e) - f(p - e)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def _net(W1, b1, W2, b2, W3, b3):
+    return [np.asarray(t, dtype=np.float64) for t in (W1, b1, W2, b2, W3, b3)]
+
+
+def test_mlp_forward_closed_forms(oracle_lib):
+    """Two weight sets whose network is a known function, on dyadic inputs (every
+    operation exact in FP64):
+    * shift and unshift: a1 = relu(f + 8) = f + 8, a2 = relu(a1 + 1) = f + 9, out = a2 - 9,
+      the identity for |f| < 8 (every bias on the path matters);
+    * absolute value: a1 = [relu(f), relu(-f)], a2 = relu(relu(f) + relu(-f)), out = |f|
+      (the first ReLU matters: without it a2 would be relu(f - f) = 0)."""
+    rng = np.random.default_rng(3)
+    f = rng.integers(-64, 65, size=(50, 7)) / 16.0
+    I7 = np.eye(7)
+    W1 = np.zeros((64, 7)); W1[:7] = I7
+    b1 = np.zeros(64); b1[:7] = 8.0
+    W2 = np.eye(64); b2 = np.zeros(64); b2[:7] = 1.0
+    W3 = np.zeros((7, 64)); W3[:, :7] = I7
+    b3 = np.full(7, -9.0)
+    assert np.array_equal(O.mlp_forward(f, *_net(W1, b1, W2, b2, W3, b3)), f)
+    W1 = np.zeros((64, 7)); W1[:7] = I7; W1[7:14] = -I7
+    W2 = np.zeros((64, 64)); W2[np.arange(7), np.arange(7)] = 1.0; W2[np.arange(7), np.arange(7) + 7] = 1.0
+    W3 = np.zeros((7, 64)); W3[:, :7] = I7
+    out = O.mlp_forward(f, *_net(W1, np.zeros(64), W2, np.zeros(64), W3, np.zeros(7)))
+    assert np.array_equal(out, np.abs(f))
 
 
 def _pattern_problem():

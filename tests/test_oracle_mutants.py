@@ -18,8 +18,17 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cbg_oracle.c")
-PIN_FILES = [os.path.join(ROOT, "tests", f)
-             for f in ("test_oracle_codec.py", "test_oracle_gmres.py", "test_oracle_learned.py")]
+PIN_FILES = {k: os.path.join(ROOT, "tests", f"test_oracle_{k}.py")
+             for k in ("codec", "gmres", "learned")}
+CODEC = {  # mistakes in the codec: test_oracle_codec.py runs first
+    "bf16_max_overflows", "bf16_precision", "e4m3_nan_exponent", "e4m3_no_saturation",
+    "e4m3_scale_fmax", "f16_decode_bias", "f16_emin", "f16_max_overflows",
+    "int_decode_scale", "int_sigma", "int_truncates", "pow2_scale_not_smallest",
+    "round_ties_away", "round_truncates", "subnormal_pack_shift"}
+LEARNED = {  # mistakes in the network and SPAI parts: test_oracle_learned.py runs first
+    "mlp_forward_no_bias", "mlp_forward_no_relu", "mlp_relu_grad", "mlp_w2_transposed",
+    "mlp_w3_grad_operand", "spai_gradient_factor", "spai_loss_cross_term",
+    "spai_slots_swapped", "spai_statistic_d"}
 
 # (name, what the mistake is, exact snippet of cbg_oracle.c, its replacement)
 MUTANTS = [
@@ -113,6 +122,60 @@ MUTANTS = [
     ("spai_loss_cross_term", "SPAI loss cross term without its factor 2",
      "li += pv[k] * gp - 2.0 * pv[k] * c[i * 7 + k];",
      "li += pv[k] * gp - pv[k] * c[i * 7 + k];"),
+    ("conditional_reorth_inverted", "conditional re-orthogonalisation when ||w|| >= eta omega",
+     "(a->reorth == OR_REORTH_CONDITIONAL && hn < a->eta * omega);",
+     "(a->reorth == OR_REORTH_CONDITIONAL && hn >= a->eta * omega);"),
+    ("breakdown_unscaled", "breakdown test against eps instead of eps omega",
+     "int stop = !(hn > a->eps_bd * omega);",
+     "int stop = !(hn > a->eps_bd);"),
+    ("omega_of_z", "omega taken from M^{-1} v_j instead of w = A M^{-1} v_j",
+     "double omega = nrm2(n, w);",
+     "double omega = nrm2(n, z);"),
+    ("adapt_condition_inverted", "adaptive switch when the explicit residual is below the gap",
+     "if (a->adapt && a->cycles > 0 && beta > a->adapt_gap * last_est) {",
+     "if (a->adapt && a->cycles > 0 && beta < a->adapt_gap * last_est) {"),
+    ("residual_estimate_index", "recurrence residual read from g_j instead of g_{j+1}",
+     "double est = fabs(g[j + 1]);",
+     "double est = fabs(g[j]);"),
+    ("restart_discards_x", "restart replaces x by the last correction",
+     "for (int64_t t = 0; t < n; t++) x[t] += z[t];",
+     "for (int64_t t = 0; t < n; t++) x[t] = z[t];"),
+    ("f16_max_overflows", "binary16 65504 encoded as infinity",
+     "if (fabs(r) > 65504.0) return (uint16_t)(sign | 0x7C00u);",
+     "if (fabs(r) >= 65504.0) return (uint16_t)(sign | 0x7C00u);"),
+    ("bf16_max_overflows", "bfloat16 largest finite value encoded as infinity",
+     "if (fabs(r) > 0x1.FEp127) return (uint16_t)(sign | 0x7F80u);",
+     "if (fabs(r) >= 0x1.FEp127) return (uint16_t)(sign | 0x7F80u);"),
+    ("e4m3_nan_exponent", "e4m3 decode treats every exponent-15 pattern as NaN (IEEE-style)",
+     "if (expf == 0xFu && man == 0x7u) return NAN;",
+     "if (expf == 0xFu) return NAN;"),
+    ("subnormal_pack_shift", "subnormal mantissa packed one bit low",
+     "man = (uint32_t)ldexp(a, mbits - emin);",
+     "man = (uint32_t)ldexp(a, mbits - emin - 1);"),
+    ("e4m3_scale_fmax", "e4m3 scale chosen for a maximum of 256 instead of 448",
+     "int e = pow2_scale_exponent(vmax, fmt == OR_BF16 ? 1.0 : 448.0);",
+     "int e = pow2_scale_exponent(vmax, fmt == OR_BF16 ? 1.0 : 256.0);"),
+    ("bj4_elimination_sign", "Gauss-Jordan elimination adds the pivot row",
+     "for (int c = 0; c < 2 * kb; c++) aug[i][c] = aug[i][c] - f * aug[k][c];",
+     "for (int c = 0; c < 2 * kb; c++) aug[i][c] = aug[i][c] + f * aug[k][c];"),
+    ("mlp_forward_no_bias", "network forward drops the first layer's bias",
+     "double s = b1[o];",
+     "double s = 0.0;"),
+    ("mlp_forward_no_relu", "network forward without the first ReLU",
+     "a1[o] = s > 0.0 ? s : 0.0;",
+     "a1[o] = s;"),
+    ("mlp_w3_grad_operand", "W3 gradient multiplies by the first hidden layer",
+     "for (int i = 0; i < MLP_H; i++) gW3[o * MLP_H + i] += go[o] * a2[i];",
+     "for (int i = 0; i < MLP_H; i++) gW3[o * MLP_H + i] += go[o] * a1[i];"),
+    ("spai_slots_swapped", "stencil slots of the -x and -y neighbours swapped",
+     "const int64_t off[7] = {-sxy, -sx, -1, 0, 1, sx, sxy};",
+     "const int64_t off[7] = {-sx, -sxy, -1, 0, 1, sx, sxy};"),
+    ("spai_statistic_d", "pair statistic d without the square of e",
+     "d[i] += wgt * e[i] * e[i];",
+     "d[i] += wgt * e[i];"),
+    ("spai_gradient_factor", "SPAI loss gradient without its factor 2",
+     "if (gout) gout[i * 7 + k] = has[k] ? 2.0 * (gp - c[i * 7 + k]) / diag[i] / npairs : 0.0;",
+     "if (gout) gout[i * 7 + k] = has[k] ? (gp - c[i * 7 + k]) / diag[i] / npairs : 0.0;"),
 ]
 
 
@@ -131,12 +194,24 @@ def _build(src_text, path):
     return path
 
 
-def _run_pins(lib_path):
+def _region(name):
+    return "codec" if name in CODEC else "learned" if name in LEARNED else "gmres"
+
+
+def _run_pins(lib_path, first):
+    """Exit status of the pin files against the library: the file of the mistake's own
+    region first, the other two only if it passes (0: every pin passed, 1: one failed)."""
     env = dict(os.environ, CBG_ORACLE_LIB=lib_path, OMP_NUM_THREADS="2")
-    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "-m", "not gpu"] + PIN_FILES,
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    return p.returncode, p.stdout[-3000:]
+    rest = [f for k, f in PIN_FILES.items() if k != first]
+    out = ""
+    for files in ([PIN_FILES[first]], rest):
+        p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            "-m", "not gpu"] + files,
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+        out += p.stdout[-1500:]
+        if p.returncode != 0:
+            return p.returncode, out
+    return 0, out
 
 
 @pytest.fixture(scope="module")
@@ -144,13 +219,14 @@ def outcomes(tmp_path_factory):
     src = open(SRC).read()
     d = str(tmp_path_factory.mktemp("oracle_mutants"))
     jobs = {"control": src}
+    assert CODEC | LEARNED <= {m[0] for m in MUTANTS}
     for name, _, old, new in MUTANTS:
         assert src.count(old) == 1, f"{name}: snippet not found exactly once in cbg_oracle.c"
         jobs[name] = src.replace(old, new)
 
     def one(item):
         name, text = item
-        return name, _run_pins(_build(text, os.path.join(d, f"lib_{name}.so")))
+        return name, _run_pins(_build(text, os.path.join(d, f"lib_{name}.so")), _region(name))
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         return dict(ex.map(one, jobs.items()))
