@@ -254,7 +254,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------ CPU baseline helpers
 def host_cpu() -> dict:
-    """Host threads and CPU model of this machine (the GPU machine's host when run there)."""
+    """Host threads and CPU model of the machine this process runs on."""
     model = None
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -589,8 +589,8 @@ def run_random27(args):
             A01, b01 = A, bnp
     clk = clocks.stop()
     t = {f: results[f]["ms"] for f in fmts}
-    # each format against the oracle's solution (the benchmark spec: the error against the FP64
-    # oracle per format), and the oracle's time-to-solution as the CPU baseline
+    # each format's error against the oracle's FP64 solution, stated per format, and the
+    # oracle's time-to-solution as the CPU baseline
     hc = host_cpu()
     per_fmt = {}
     t_oracle = {}

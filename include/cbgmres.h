@@ -92,7 +92,7 @@ typedef enum { CBG_ORTHO_CGS = 0, CBG_ORTHO_MGS = 1 } cbg_ortho;
  *   prescribes; on GB300 the basis products then run at FP64-pipe speed.
  * With CBG_ARITH_DF32 the norms of the Arnoldi step (omega = ||A v_j|| in the SpMV,
  * ||w|| in the last CGS pass) are also summed in double-float per thread and combined
- * in FP64.  The residual SpMV (b - Ax, the convergence judge), ||r||, the Givens
+ * in FP64.  The residual SpMV (b - Ax, which decides convergence), ||r||, the Givens
  * rotations, the least-squares solve and the solution update are FP64 in both modes. */
 typedef enum { CBG_ARITH_DF32 = 0, CBG_ARITH_FP64 = 1 } cbg_arith;
 
@@ -387,7 +387,7 @@ void cbgmres_destroy_batched(cbg_batch* bt);
 
 /* Try the handles in order (e.g. learned SPAI, Jacobi, none -- all for the same A),
  * each continuing from the current x, until one reaches ||b - A x|| <= tol ||b||: the
- * FP64 explicit residual is the judge.  A handle whose solve ends non-converged or
+ * FP64 explicit residual decides.  A handle whose solve ends non-converged or
  * stagnated hands over its x; one that produces non-finite values hands over the x it
  * started from.  maxit caps the total Arnoldi steps.  *used = index of the handle that
  * converged (or the last one tried).  stats accumulates over the attempts. */

@@ -2,7 +2,7 @@
 (BF16 operands, FP32 accumulation) against the FP64 oracle on the same BF16-rounded
 weights, and against a numpy restatement that rounds the same operands to BF16; the pair
 statistics and loss against the oracle's; and what training buys in GMRES iterations
-(vs. no preconditioner and vs. Jacobi), with the fallback chain judged by the true
+(vs. no preconditioner and vs. Jacobi), with the fallback chain decided by the true
 residual.
 
 Bars: against the FP64 oracle, the network's outputs and the loss within 2e-2

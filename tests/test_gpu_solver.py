@@ -79,7 +79,7 @@ def test_conditional_reorth_parity(fmt, eta):
 def test_mgs_hessenberg_and_solve_parity(fmt, reorth, arith):
     """Modified Gram-Schmidt (the variant Section 2 names): the first 10 Hessenberg
     columns against the oracle's MGS, then the full solve: iterations within 2 %, x within
-    1e-6 of the oracle's, true residual judged by the oracle's SpMV.  (Without the second
+    1e-6 of the oracle's, true residual checked with the oracle's SpMV.  (Without the second
     pass the 16-bit bases' iteration counts depend on rounding, as CGS and MGS differ
     there by 8-15 % in the oracle itself, so those pairs are not asked to match to 2 %.)"""
     torch, cb = need_gpu()
@@ -112,7 +112,7 @@ def test_operator_scale_and_range(case, arith):
     power of two and scales the Hessenberg columns back), or with every 50th off-diagonal
     nonzero times 2^-80 (a dynamic range beyond 2^64: FP64 products in the per-step SpMV): the
     first Hessenberg columns against the oracle on the same matrix, and the solve to 1e-10
-    judged by the oracle's SpMV."""
+    checked with the oracle's SpMV."""
     torch, cb = need_gpu()
     A0, xs, _ = _problem("convdiff20")
     A = scaled_matrix(A0, case)
@@ -145,7 +145,7 @@ def test_full_solve_parity(prob, fmt):
         st = s.solve(to_dev(torch, b), xg, tol=tol, maxit=maxit)
     assert st["status"] == 0, st
     x = xg.cpu().numpy()
-    # the oracle judges the GPU's answer
+    # the oracle checks the GPU's answer
     r = b - O.spmv(A, x)
     assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * (1 + 1e-9)
     assert abs(st["iters"] - ro["iters"]) <= max(1, 0.02 * ro["iters"]), (st["iters"], ro["iters"])
@@ -158,7 +158,7 @@ def test_long_restart_parity(m, fmt):
     """Restart lengths of the paper's restart sweep (Section 5.4 goes to m = 300): Poisson
     128 x 128 needs 250 and 300 steps in its first cycle, so the basis products run with
     up to m + 1 = 301 columns.  The first 10 Hessenberg columns, then the full solve:
-    iterations within 2 % of the oracle's, x within 1e-6, true residual judged by the
+    iterations within 2 % of the oracle's, x within 1e-6, true residual checked with the
     oracle's SpMV."""
     torch, cb = need_gpu()
     A, xs, b = _problem("poisson128")
