@@ -47,3 +47,21 @@ def test_kernel_class_table_shares_and_rates():
     assert abs(t["basis_dot"]["share"] - 0.75) < 1e-12
     assert t["spmv"]["us_per_launch"] == 20.0
     assert t["basis_dot"]["gbs"] == 5000.0 and t["spmv"]["gbs"] == 4000.0
+
+
+def test_clock_record_from_nvidia_smi_lines():
+    import bench
+    lines = [
+        "0, 2070, 2070, 850.10, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 900.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",     # unreadable sample: skipped
+        "index, clocks.sm",                                              # stray header: skipped
+    ]
+    r = bench.parse_clock_lines(lines)
+    assert r["samples"] == 3 and r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["power_w_max"] == 1390.0 and r["reasons"] == ["sw_power_cap"]
+    r = bench.parse_clock_lines(lines[:1] + [
+        "0, 1500, 2070, 700.0, 0x0000000000000008, Active, Not Active, Active, Not Active"])
+    assert r["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.parse_clock_lines([])["sm_mhz"] is None
