@@ -20,7 +20,12 @@
  *     stream); calls that return results to the host synchronise that stream.
  *   - Every function returns an int status (CBG_OK = 0).  Positive values are
  *     non-fatal (x still holds the best iterate); negative values are errors and leave
- *     outputs unspecified.  Nothing throws across the ABI.
+ *     outputs unspecified.  Nothing throws across the ABI.  Where an entry point lists no
+ *     errors of its own: CBG_ERR_ARG for a null handle or pointer or a size out of range,
+ *     CBG_ERR_CUDA when a CUDA call fails (cbgmres_last_error names it).
+ *   - Ownership: the library never keeps or frees caller memory; buffers passed in are
+ *     read or written during the call (or, for asynchronous calls, until the stream
+ *     reaches that work).  A handle owns its device allocations until its destroy call.
  *   - A handle may be used by one host thread at a time.
  */
 #ifndef CBGMRES_H
@@ -222,7 +227,10 @@ int cbgmres_set_spai(cbg_handle* h, const double* pvals, int on_device);
 /* Solve A x = b.  b, x: device pointers (length n).  x holds x0 on entry and the
  * final iterate on exit.  Stops when ||b - A x|| <= tol ||b|| (explicit residual,
  * Section 5.2) or after maxit Arnoldi steps (CBG_NOT_CONVERGED).  stats may be NULL.
- * Synchronises options.stream once per restart (to read the explicit residual). */
+ * Synchronises options.stream once per restart (to read the explicit residual).
+ * Errors: CBG_ERR_ARG (null pointers, CBG_PC_SPAI without cbgmres_set_spai),
+ * CBG_ERR_NONFINITE (NaN/Inf in b, x0 or produced by the iteration), CBG_ERR_TIMEOUT (a
+ * bounded device wait ran out; the handle stays usable), CBG_ERR_CUDA. */
 int cbgmres_solve(cbg_handle* h, const double* b, double* x, double tol, int64_t maxit,
                   cbg_stats* stats);
 
