@@ -584,7 +584,7 @@ def run_random27(args):
             for f in fmts:
                 s = cb.Solver.from_csr(A, restart=m, fmt=f, profile=True)
                 reps = args.steps if timed_cfg else 1
-                for _ in range(args.warmup if timed_cfg else 0):
+                for _ in range(args.warmup):      # every configuration, so each row's time is warm
                     timed_solve(s, b, x, tol, args.maxit, stream)
                 s.profile(reset=True)
                 ts = []
@@ -775,11 +775,15 @@ def run_restart_sweep(args):
         t = {}
         for f in fmts:
             s = cb.Solver.from_csr(A, restart=m, fmt=f, profile=True)
-            timed_solve(s, b, x, 0.0, 10 * m, stream)
+            for _ in range(args.warmup):
+                timed_solve(s, b, x, 0.0, 10 * m, stream)
             s.profile(reset=True)
-            tt, st = timed_solve(s, b, x, 0.0, 10 * m, stream)
-            launches += st["kernel_launches"]
-            t[f] = tt
+            ts = []
+            for _ in range(args.steps):
+                tt, st = timed_solve(s, b, x, 0.0, 10 * m, stream)
+                launches += st["kernel_launches"]
+                ts.append(tt)
+            t[f] = sum(ts) / len(ts)
             if m == 300 and f == "f32":
                 roof = roofline_from_profile(s.profile(), "f32, m 300",
                                              {"basis_dot": "k_basis_dot_tma", "basis_axpy": "k_basis_axpy"}, peak, kind)
@@ -798,11 +802,12 @@ def run_restart_sweep(args):
         cpu = cpu_line(s_all * 1000, s_one * 1000, t100,
                        "oracle, m = 100, f32 basis: one full restart cycle on all host threads, the first 25 "
                        "steps on 1 thread; the 10 fixed cycles (1000 steps) extrapolated", hc, True)
-    e2e = e2e_host_ratio(keep, "f64", "f32", bnp, A.n, 0.0, 1000, 1)
+    e2e = e2e_host_ratio(keep, "f64", "f32", bnp, A.n, 0.0, 1000, args.steps)
     for s in keep.values():
         s.close()
     line = {"metric": METRIC, "value": rows[-1]["speedup_vs_f64"]["f32"], "unit": "x", "n_gpus": 1,
-            "steps": 1, "warmup": 1, "ms_per_step": round(sum(sum(r["ms"].values()) for r in rows), 3),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sum(sum(r["ms"].values()) for r in rows), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
             "config": {"workload": f"restart_sweep_{WORKLOAD}", "cycles": 10,
                        "value_is": "time(f64 basis) / time(f32 basis) at m = 300; rows: every m and format",
